@@ -1,0 +1,191 @@
+/*
+ * tlbm: GB300 (sm_103a) thermal lattice Boltzmann step, C ABI.
+ *
+ * The library advances the double-distribution-function (DDF) thermal lattice
+ * Boltzmann model of Xu & Li, "Multi-GPU thermal lattice Boltzmann simulations
+ * using OpenACC and MPI" (IJHMT 2022):
+ *   - flow populations f on D2Q9 / D3Q19 with the MRT collision of Eq. (5)
+ *     and the Guo forcing term of Eq. (6a)/(6b);
+ *   - temperature populations g on D2Q5 / D3Q7 with the MRT collision of Eq. (7);
+ *   - Boussinesq buoyancy F = rho g beta (T - T0) along +y (2D) or +z (3D), §2.2;
+ *   - macroscopic rho = sum f, u = (sum e f + F/2)/rho, T = sum g, §2.2;
+ *   - half-way bounce-back (no-slip), half-way anti-bounce-back (isothermal,
+ *     omega = (4 + a_T)/10 or (6 + a_T)/21) and bounce-back of g (adiabatic), §2.2;
+ *   - collision and streaming, Eqs. (10)-(11), fused into one pull kernel.
+ * Parameters follow the free-fall scaling of Eqs. (2)-(4): H = cell height (ny in
+ * 2D, nz in 3D), dT = Th - Tc = 1, U = Ma/sqrt(3), nu = U H sqrt(Pr/Ra),
+ * alpha = U H / sqrt(Pr Ra), g beta = U^2 / (H dT).
+ *
+ * Conventions shared by every call:
+ *   - Every function returns TLBM_OK (0) or a negative TLBM_ERR_* code; the text
+ *     of the last error is kept per handle (tlbm_last_error).
+ *   - Kernels run asynchronously on the handle's stream.  A call that returns a
+ *     host value (nusselt, energy, status, get_populations) synchronises that
+ *     stream.  A device fault from an earlier asynchronous call is reported by
+ *     the next synchronising call as TLBM_ERR_CUDA.
+ *   - Device memory: the caller owns it.  tlbm_required_bytes() gives the size
+ *     of one block that holds both population buffers plus the library's
+ *     scratch; tlbm_bind_memory() hands it to the handle.  The library never
+ *     allocates or frees device memory for a handle.
+ *   - Arrays exchanged with the caller are dense, x fastest:
+ *     node n = x + nx*(y + ny*z); population i of a set at [i*N + n], N = nx*ny*nz.
+ *   - The state "after t steps" is the pre-collision population set at time t.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef TLBM_H
+#define TLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TLBM_API __attribute__((visibility("default")))
+#else
+#define TLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- constants */
+enum tlbm_status_code {
+    TLBM_OK = 0,
+    TLBM_ERR_ARG = -1,         /* invalid argument (bad size, NULL, out of range) */
+    TLBM_ERR_OOM = -2,         /* bound memory too small / host allocation failed */
+    TLBM_ERR_CUDA = -3,        /* a CUDA runtime call or a kernel failed */
+    TLBM_ERR_DIVERGED = -4,    /* non-finite or |u| > 0.5 found in the state */
+    TLBM_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+    TLBM_ERR_UNBOUND = -6,     /* device memory not bound yet */
+    TLBM_ERR_UNSUPPORTED = -7  /* combination not built (e.g. unknown precision) */
+};
+
+enum tlbm_lattice { TLBM_D2Q9_D2Q5 = 0, TLBM_D3Q19_D3Q7 = 1 };
+
+/* Storage precision of the populations.  FP16/BF16 "offset" storage keeps
+ * f_i - w_i (flow) and g_i (temperature, T0 = 0) scaled by a power of two;
+ * collision then runs in FP32.  FP64 storage collides in FP64. */
+enum tlbm_prec { TLBM_FP64 = 0, TLBM_FP32 = 1, TLBM_FP16_OFFSET = 2, TLBM_BF16_OFFSET = 3 };
+
+/* Wall configuration.  RB: hot bottom (Th), cold top (Tc), adiabatic sides.
+ * SIDE_HEATED (§2.3): hot left wall (x = -1/2), cold right wall, others adiabatic.
+ * Every non-periodic face is a no-slip wall. */
+enum tlbm_walls { TLBM_RB = 0, TLBM_SIDE_HEATED = 1 };
+
+/* Output element type for tlbm_macros. */
+enum tlbm_dtype { TLBM_OUT_F64 = 0, TLBM_OUT_F32 = 1 };
+
+/* Optional parameters.  Initialise with tlbm_default_params(); every double left
+ * as NaN is derived from (Ra, Pr, Ma) as stated at the top of this file:
+ *   s_nu = 1/(3 nu + 1/2) on all even non-conserved flow moments (s_e, s_eps, s_pi),
+ *   s_q = s_m = 8(2 - s_nu)/(8 - s_nu) on all odd non-conserved ones,
+ *   s_rho = s_j = 1 (they do not change the result),
+ *   a_T = -2/3 (D2Q5) or -3/4 (D3Q7), q_j from alpha = omega (1/q_j - 1/2),
+ *   q_e = q_v from (1/q_j - 1/2)(1/q_e - 1/2) = 1/4.
+ * periodic_mask (bit0 x, bit1 y, bit2 z) and body_force (a constant
+ * acceleration; force density rho*a) exist for validation cases. */
+typedef struct {
+    int walls;
+    int periodic_mask;
+    int u_is_ma;            /* 1: U = Ma instead of Ma/sqrt(3) */
+    double a_T;
+    double nu, alpha, gbeta;
+    double s_rho, s_e, s_eps, s_j, s_q, s_pi, s_m;
+    double q_e, q_v;
+    double body_force[3];
+    double Th, Tc;
+    double store_scale;     /* FP16/BF16 storage scale (power of two); NaN = default */
+} tlbm_params;
+
+typedef struct tlbm_s* tlbm_t;
+
+/* One instance of a batched ensemble (same lattice and precision for all). */
+typedef struct {
+    int nx, ny, nz;
+    double Ra, Pr, Ma;
+    uint64_t seed;
+} tlbm_instance;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Fill *p with the defaults described above (all derivable doubles NaN). */
+TLBM_API void tlbm_default_params(tlbm_params* p);
+
+/* Create a handle for an nx x ny (x nz) cell.  nz is ignored (1) for D2Q9_D2Q5.
+ * Errors: TLBM_ERR_ARG for nx, ny < 3, nz < 3 in 3D, Ra/Pr/Ma <= 0, an unknown
+ * lattice/precision/walls value, or tau - 1/2 = 3 nu <= 1e-6.  *out is set to
+ * NULL on error.  The handle owns host memory only. */
+TLBM_API int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, double Ra, double Pr,
+                double Ma, int precision, const tlbm_params* p);
+
+/* Bytes of device memory the handle needs (both population buffers and
+ * scratch), 256-byte aligned. */
+TLBM_API int tlbm_required_bytes(tlbm_t h, size_t* bytes);
+
+/* Bind a caller-owned device block of at least tlbm_required_bytes() bytes,
+ * 256-byte aligned.  The library never frees it; it must outlive the handle's
+ * use.  Re-binding moves nothing: call tlbm_init or tlbm_set_populations after. */
+TLBM_API int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes);
+
+/* Stream for all later work (a cudaStream_t; NULL = legacy default stream). */
+TLBM_API int tlbm_set_stream(tlbm_t h, void* cuda_stream);
+
+/* Initial state (t = 0): f = f_eq(rho = 1, u = 0) and g = g_eq(T, 0) with the
+ * conductive profile between the isothermal walls plus noise_amp*(2r - 1),
+ * r = (splitmix64(seed ^ splitmix64(n)) >> 11) * 2^-53 for node n. */
+TLBM_API int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp);
+
+/* Advance n >= 0 time steps (Eqs. (10)-(11), fused).  Asynchronous. */
+TLBM_API int tlbm_step(tlbm_t h, int64_t n);
+
+/* Macroscopic fields of the current state into caller device arrays of
+ * nx*ny*nz elements (x fastest), element type out_dtype.  NULL skips a field;
+ * uz is ignored in 2D.  Asynchronous. */
+TLBM_API int tlbm_macros(tlbm_t h, void* rho, void* ux, void* uy, void* uz, void* T, int out_dtype);
+
+/* Nusselt number of the current state, FP64 deterministic reduction:
+ * Nu = 1 + L <u_h T> / (alpha dT), u_h the velocity component along the
+ * heat-flux axis (vertical for RB, x for side-heated) and L the cell extent
+ * along it.  Synchronises the stream. */
+TLBM_API int tlbm_nusselt(tlbm_t h, double* nu);
+
+/* Kinetic energy sum 1/2 rho |u|^2 and mass sum rho, FP64.  Synchronises. */
+TLBM_API int tlbm_energy(tlbm_t h, double* ekin, double* mass);
+
+/* Copy the canonical pre-collision populations (FP64, dense layout above) to
+ * host arrays f[qf*N], g[qg*N] (either may be NULL).  Synchronises. */
+TLBM_API int tlbm_get_populations(tlbm_t h, double* host_f, double* host_g);
+
+/* Same for the box [x0, x0+wx) x [y0, y0+wy) x [z0, z0+wz) of the cell (z0 = 0,
+ * wz = 1 in 2D); the host arrays hold qf (qg) planes of wx*wy*wz values, x
+ * fastest.  TLBM_ERR_ARG if the box leaves the cell.  Synchronises. */
+TLBM_API int tlbm_get_populations_window(tlbm_t h, int x0, int y0, int z0, int wx, int wy, int wz,
+                                         double* host_f, double* host_g);
+
+/* Replace the state by host FP64 populations in the same layout (rounded to the
+ * storage precision).  Both pointers are required.  Synchronises. */
+TLBM_API int tlbm_set_populations(tlbm_t h, const double* host_f, const double* host_g);
+
+/* *diverged = 1 if the state holds a non-finite value or |u| > 0.5; *step =
+ * current time step.  Runs a reduction; synchronises.  Either output may be NULL. */
+TLBM_API int tlbm_status(tlbm_t h, int* diverged, int64_t* step);
+
+/* Derived parameters: out[0..6] = U, H, nu, alpha, gbeta, a_T, omega, then the
+ * flow rates S[qf] and thermal rates Q[qg].  Returns the count written (<= cap)
+ * through *count. */
+TLBM_API int tlbm_derived(tlbm_t h, double* out, int cap, int* count);
+
+/* Text of the last error on this handle ("" if none); valid until the next call
+ * on the handle.  A NULL handle returns the last error of a failed tlbm_create
+ * in this thread. */
+TLBM_API const char* tlbm_last_error(tlbm_t h);
+
+/* Number of kernels this handle has launched so far (for accounting). */
+TLBM_API int tlbm_launch_count(tlbm_t h, int64_t* count);
+
+TLBM_API void tlbm_destroy(tlbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLBM_H */

@@ -1,0 +1,747 @@
+// C ABI of the thermal lattice Boltzmann library (declared in include/tlbm.h):
+// handle lifecycle, parameter mapping, memory binding, launches of the fused
+// step, and the initial-state, population transfer, macro and reduction kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/tlbm.h"
+#include "dispatch.h"
+
+using namespace tlbm;
+
+namespace {
+
+constexpr int RED_BLOCKS = 1024;   // fixed reduction grid: the summation order never changes
+constexpr int RED_THREADS = 256;
+constexpr int RED_FIELDS = 6;      // sum u_h T, sum 1/2 rho u^2, sum rho, max u^2, bad, sum T
+constexpr long long STAGE_NODES = 1ll << 21;  // FP64 staging chunk for population transfers
+
+thread_local char g_create_error[256] = "";
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct tlbm_s {
+    int nx, ny, nz, dim, lattice, prec;
+    int qf, qg;
+    double Ra, Pr, Ma;
+    tlbm_params prm;
+    double U, H, nu, alpha, gbeta, a_T, omega;
+    double S[MAXQ], Q[7];
+    KParams kp;
+    size_t elem;               // bytes per stored value
+    size_t popset_bytes;       // one population buffer (f planes then g planes)
+    size_t red_off, res_off, stage_off, total_bytes;
+    char* mem;                 // bound device block
+    size_t mem_bytes;
+    void* buf[2];
+    int cur;                   // buffer holding the current state
+    int64_t t;
+    cudaStream_t stream;
+    int64_t launches;
+    char err[256];
+};
+
+// ------------------------------------------------------------------ errors
+
+static int fail(tlbm_t h, int code, const char* fmt, ...) {
+    char* dst = h ? h->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(tlbm_t h, cudaError_t e, const char* what) {
+    return fail(h, TLBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define TLBM_CHECK_HANDLE(h)                                   \
+    do {                                                       \
+        if (!(h)) return fail(nullptr, TLBM_ERR_ARG, "NULL handle"); \
+        (h)->err[0] = 0;                                       \
+    } while (0)
+
+#define TLBM_CHECK_BOUND(h)                                                         \
+    do {                                                                            \
+        if (!(h)->mem) return fail((h), TLBM_ERR_UNBOUND, "device memory not bound"); \
+    } while (0)
+
+// ------------------------------------------------------------------ kernels
+
+namespace {
+
+// splitmix64 output function (Steele, Lea & Flood 2014).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// A box of nodes [x0, x0 + wx) x [y0, y0 + wy) x [z0, z0 + wz), enumerated x fastest.
+struct Window {
+    int x0, y0, z0, wx, wy, wz;
+};
+
+__device__ __forceinline__ void window_xyz(long long k, const Window& w, int& x, int& y, int& z) {
+    x = w.x0 + (int)(k % w.wx);
+    long long r = k / w.wx;
+    y = w.y0 + (int)(r % w.wy);
+    z = w.z0 + (int)(r / w.wy);
+}
+
+__device__ __forceinline__ void node_xyz(long long n, const Layout& L, int& x, int& y, int& z) {
+    x = (int)(n % L.nx);
+    long long r = n / L.nx;
+    y = (int)(r % L.ny);
+    z = (int)(r / L.ny);
+}
+
+// Initial state: f = w (rho = 1, u = 0), g = g_eq(T, 0) with the conductive
+// profile plus seeded uniform noise.  Every pre-collision value f_i(x) is
+// written into the slot x - e_i it is pulled from.
+template <int DIM, class S>
+__global__ void init_kernel(S* __restrict__ buf, const KParams p, uint64_t seed, double amp) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    using C = typename Storage<S>::C;
+    const Layout& L = p.L;
+    const long long N = (long long)L.nx * L.ny * L.nz;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        node_xyz(n, L, x, y, z);
+        const int c = p.heat_axis == 0 ? x : (p.heat_axis == 1 ? y : z);
+        const int len = p.heat_axis == 0 ? L.nx : (p.heat_axis == 1 ? L.ny : L.nz);
+        const double r = (double)(splitmix64(seed ^ splitmix64((uint64_t)n)) >> 11) * 0x1.0p-53;
+        double T = __dadd_rn(p.Th, __dmul_rn(p.Tc - p.Th, __ddiv_rn((double)c + 0.5, (double)len)));
+        T = __dadd_rn(T, __dmul_rn(amp, 2.0 * r - 1.0));
+        double nm[LG::Q];
+        for (int k = 0; k < LG::Q; ++k) nm[k] = 0.0;
+        nm[0] = T;
+        nm[DIM == 2 ? 3 : 4] = p.a_T * T;
+        double gq[LG::Q];
+        populations<LG, double>(nm, gq);
+        const C scale = (C)p.scale;
+        static_for<LF::Q>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            buf[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))] =
+                enc_f<LF, S, C>(C(0), i, scale);
+        });
+        S* gb = buf + (long long)LF::Q * L.plane;
+        static_for<LG::Q>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            gb[(long long)i * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))] =
+                enc_g<S, C>((C)gq[i], scale);
+        });
+    }
+}
+
+// Host FP64 populations (one plane, nodes [n0, n0 + cnt)) -> pull slots.
+template <int DIM, class S>
+__global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ stage, int pop, long long n0,
+                               long long cnt, const Window w, const KParams p) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    using C = typename Storage<S>::C;
+    const Layout& L = p.L;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < cnt;
+         k += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        window_xyz(n0 + k, w, x, y, z);
+        const double v = stage[k];
+        static_for<LF::Q>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            if (pop == i) {
+                S s;
+                if constexpr (Storage<S>::offset) s = from_c<S>((C)((v - LF::w36(i) / 36.0) * p.scale));
+                else s = (S)v;
+                buf[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))] = s;
+            }
+        });
+        static_for<LG::Q>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            if (pop == LF::Q + i) {
+                S s;
+                if constexpr (Storage<S>::offset) s = from_c<S>((C)(v * p.scale));
+                else s = (S)v;
+                buf[(long long)(LF::Q + i) * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))] = s;
+            }
+        });
+    }
+}
+
+// Pull slots -> canonical FP64 populations (one plane, nodes [n0, n0 + cnt)).
+template <int DIM, class S>
+__global__ void gather_kernel(const S* __restrict__ buf, double* __restrict__ stage, int pop, long long n0,
+                              long long cnt, const Window w, const KParams p) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    const Layout& L = p.L;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < cnt;
+         k += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        window_xyz(n0 + k, w, x, y, z);
+        double v = 0.0;
+        static_for<LF::Q>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            if (pop == i) {
+                const double raw = to_c<double>(
+                    buf[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))]);
+                if constexpr (Storage<S>::offset) v = LF::w36(i) / 36.0 + raw * (double)p.inv_scale;
+                else v = raw;
+            }
+        });
+        static_for<LG::Q>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            if (pop == LF::Q + i) {
+                const double raw = to_c<double>(
+                    buf[(long long)(LF::Q + i) * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))]);
+                if constexpr (Storage<S>::offset) v = raw * (double)p.inv_scale;
+                else v = raw;
+            }
+        });
+        stage[k] = v;
+    }
+}
+
+// rho, u, T of the current state into dense caller arrays.
+template <int DIM, class S, class O>
+__global__ void macros_kernel(const S* __restrict__ buf, const KParams p, O* rho, O* ux, O* uy, O* uz, O* T) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    const Layout& L = p.L;
+    const long long N = (long long)L.nx * L.ny * L.nz;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        node_xyz(n, L, x, y, z);
+        double f[LF::Q], g[LG::Q], r, u[3], t;
+        pull_node<DIM, S, double>(buf, p, x, y, z, f, g);
+        node_macros<DIM, double>(f, g, p, r, u, t);
+        if (rho) rho[n] = (O)r;
+        if (ux) ux[n] = (O)u[0];
+        if (uy) uy[n] = (O)u[1];
+        if (uz) uz[n] = (O)u[2];
+        if (T) T[n] = (O)t;
+    }
+}
+
+// Deterministic FP64 reduction, pass 1: each block sums a fixed node subset in
+// a fixed order (per-thread serial loop, then a fixed warp-shuffle tree and a
+// fixed cross-warp order) and writes its partials.
+template <int DIM, class S>
+__global__ void __launch_bounds__(RED_THREADS) reduce_kernel(const S* __restrict__ buf, const KParams p,
+                                                            double* __restrict__ partials) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    const Layout& L = p.L;
+    const long long N = (long long)L.nx * L.ny * L.nz;
+    double acc[RED_FIELDS] = {0, 0, 0, 0, 0, 0};
+    for (long long n = blockIdx.x * (long long)RED_THREADS + threadIdx.x; n < N;
+         n += (long long)RED_BLOCKS * RED_THREADS) {
+        int x, y, z;
+        node_xyz(n, L, x, y, z);
+        double f[LF::Q], g[LG::Q], r, u[3], t;
+        pull_node<DIM, S, double>(buf, p, x, y, z, f, g);
+        node_macros<DIM, double>(f, g, p, r, u, t);
+        const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        acc[0] += u[p.heat_axis] * t;
+        acc[1] += 0.5 * r * u2;
+        acc[2] += r;
+        acc[3] = fmax(acc[3], u2);
+        if (!isfinite(r) || !isfinite(t) || !isfinite(u2)) acc[4] = 1.0;
+        acc[5] += t;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < RED_FIELDS; ++k) {
+            const double o = __shfl_down_sync(0xffffffffu, acc[k], off);
+            acc[k] = (k == 3 || k == 4) ? fmax(acc[k], o) : acc[k] + o;
+        }
+    }
+    __shared__ double sm[RED_THREADS / 32][RED_FIELDS];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < RED_FIELDS; ++k) sm[w][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double out[RED_FIELDS];
+        for (int k = 0; k < RED_FIELDS; ++k) out[k] = sm[0][k];
+        for (int j = 1; j < RED_THREADS / 32; ++j)
+            for (int k = 0; k < RED_FIELDS; ++k)
+                out[k] = (k == 3 || k == 4) ? fmax(out[k], sm[j][k]) : out[k] + sm[j][k];
+        for (int k = 0; k < RED_FIELDS; ++k) partials[(long long)blockIdx.x * RED_FIELDS + k] = out[k];
+    }
+}
+
+// Pass 2: one block combines the RED_BLOCKS partials in a fixed tree.
+__global__ void __launch_bounds__(RED_BLOCKS) reduce_final_kernel(const double* __restrict__ partials,
+                                                                 double* __restrict__ out) {
+    __shared__ double sm[RED_BLOCKS];
+    for (int k = 0; k < RED_FIELDS; ++k) {
+        sm[threadIdx.x] = partials[(long long)threadIdx.x * RED_FIELDS + k];
+        __syncthreads();
+        for (int s = RED_BLOCKS / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s)
+                sm[threadIdx.x] = (k == 3 || k == 4) ? fmax(sm[threadIdx.x], sm[threadIdx.x + s])
+                                                     : sm[threadIdx.x] + sm[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = sm[0];
+        __syncthreads();
+    }
+}
+
+template <int DIM, class S>
+struct DiagKernels {
+    static cudaError_t init(void* buf, const KParams& p, uint64_t seed, double amp, cudaStream_t s) {
+        init_kernel<DIM, S><<<2048, 256, 0, s>>>((S*)buf, p, seed, amp);
+        return cudaGetLastError();
+    }
+    static cudaError_t scatter(void* buf, const double* st, int pop, long long n0, long long cnt, const Window& w,
+                               const KParams& p, cudaStream_t s) {
+        scatter_kernel<DIM, S><<<1024, 256, 0, s>>>((S*)buf, st, pop, n0, cnt, w, p);
+        return cudaGetLastError();
+    }
+    static cudaError_t gather(const void* buf, double* st, int pop, long long n0, long long cnt, const Window& w,
+                              const KParams& p, cudaStream_t s) {
+        gather_kernel<DIM, S><<<1024, 256, 0, s>>>((const S*)buf, st, pop, n0, cnt, w, p);
+        return cudaGetLastError();
+    }
+    static cudaError_t macros(const void* buf, const KParams& p, void* r, void* ux, void* uy, void* uz, void* T,
+                              int dt, cudaStream_t s) {
+        if (dt == TLBM_OUT_F64)
+            macros_kernel<DIM, S, double><<<2048, 256, 0, s>>>((const S*)buf, p, (double*)r, (double*)ux,
+                                                               (double*)uy, (double*)uz, (double*)T);
+        else
+            macros_kernel<DIM, S, float><<<2048, 256, 0, s>>>((const S*)buf, p, (float*)r, (float*)ux,
+                                                              (float*)uy, (float*)uz, (float*)T);
+        return cudaGetLastError();
+    }
+    static cudaError_t reduce(const void* buf, const KParams& p, double* partials, double* out, cudaStream_t s) {
+        reduce_kernel<DIM, S><<<RED_BLOCKS, RED_THREADS, 0, s>>>((const S*)buf, p, partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        reduce_final_kernel<<<1, RED_BLOCKS, 0, s>>>(partials, out);
+        return cudaGetLastError();
+    }
+};
+
+// dispatch a diagnostic call over (dim, precision)
+template <class F>
+cudaError_t with_types(int dim, int prec, F&& f) {
+    if (dim == 2) {
+        switch (prec) {
+        case TLBM_FP64: return f(DiagKernels<2, double>{});
+        case TLBM_FP32: return f(DiagKernels<2, float>{});
+        case TLBM_FP16_OFFSET: return f(DiagKernels<2, __half>{});
+        default: return f(DiagKernels<2, __nv_bfloat16>{});
+        }
+    }
+    switch (prec) {
+    case TLBM_FP64: return f(DiagKernels<3, double>{});
+    case TLBM_FP32: return f(DiagKernels<3, float>{});
+    case TLBM_FP16_OFFSET: return f(DiagKernels<3, __half>{});
+    default: return f(DiagKernels<3, __nv_bfloat16>{});
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ setup
+
+extern "C" void tlbm_default_params(tlbm_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->walls = TLBM_RB;
+    const double nan = std::nan("");
+    p->a_T = p->nu = p->alpha = p->gbeta = nan;
+    p->s_rho = p->s_e = p->s_eps = p->s_j = p->s_q = p->s_pi = p->s_m = nan;
+    p->q_e = p->q_v = nan;
+    p->Th = p->Tc = nan;
+    p->store_scale = nan;
+}
+
+static double pick(double v, double d) { return std::isnan(v) ? d : v; }
+
+extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, double Ra, double Pr, double Ma,
+                           int precision, const tlbm_params* pin) {
+    g_create_error[0] = 0;
+    if (!out) return fail(nullptr, TLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (lattice != TLBM_D2Q9_D2Q5 && lattice != TLBM_D3Q19_D3Q7)
+        return fail(nullptr, TLBM_ERR_ARG, "unknown lattice %d", lattice);
+    if (precision < TLBM_FP64 || precision > TLBM_BF16_OFFSET)
+        return fail(nullptr, TLBM_ERR_UNSUPPORTED, "unknown precision %d", precision);
+    const int dim = lattice == TLBM_D2Q9_D2Q5 ? 2 : 3;
+    if (dim == 2) nz = 1;
+    if (nx < 3 || ny < 3 || (dim == 3 && nz < 3))
+        return fail(nullptr, TLBM_ERR_ARG, "grid %d x %d x %d too small (each extent >= 3)", nx, ny, nz);
+    if (nx > (1 << 24) || ny > 65535 || nz > 65535 || (double)nx * ny * nz > 4e10)
+        return fail(nullptr, TLBM_ERR_ARG, "grid too large (nx <= 2^24, ny and nz <= 65535)");
+    if (!(Ra > 0) || !(Pr > 0) || !(Ma > 0))
+        return fail(nullptr, TLBM_ERR_ARG, "Ra, Pr and Ma must be > 0");
+    tlbm_params prm;
+    if (pin) prm = *pin;
+    else tlbm_default_params(&prm);
+    if (prm.walls != TLBM_RB && prm.walls != TLBM_SIDE_HEATED)
+        return fail(nullptr, TLBM_ERR_ARG, "unknown walls %d", prm.walls);
+    if (prm.periodic_mask < 0 || prm.periodic_mask > 7)
+        return fail(nullptr, TLBM_ERR_ARG, "periodic_mask out of range");
+
+    tlbm_s* h = new (std::nothrow) tlbm_s();
+    if (!h) return fail(nullptr, TLBM_ERR_OOM, "host allocation failed");
+    h->nx = nx; h->ny = ny; h->nz = nz; h->dim = dim; h->lattice = lattice; h->prec = precision;
+    h->qf = dim == 2 ? 9 : 19;
+    h->qg = dim == 2 ? 5 : 7;
+    h->Ra = Ra; h->Pr = Pr; h->Ma = Ma;
+    h->prm = prm;
+
+    // free-fall scaling, Eqs. (2)-(4)
+    h->prm.Th = pick(prm.Th, 0.5);
+    h->prm.Tc = pick(prm.Tc, -0.5);
+    const double dT = h->prm.Th - h->prm.Tc;
+    h->U = prm.u_is_ma ? Ma : Ma / std::sqrt(3.0);
+    h->H = dim == 2 ? ny : nz;
+    h->nu = pick(prm.nu, h->U * h->H * std::sqrt(Pr / Ra));
+    h->alpha = pick(prm.alpha, h->U * h->H / std::sqrt(Pr * Ra));
+    h->gbeta = pick(prm.gbeta, h->U * h->U / (h->H * dT));
+    h->a_T = pick(prm.a_T, dim == 2 ? -2.0 / 3.0 : -0.75);
+    h->omega = dim == 2 ? (4.0 + h->a_T) / 10.0 : (6.0 + h->a_T) / 21.0;
+    if (!(3.0 * h->nu > 1e-6) || !(h->alpha > 0) || !(h->omega > 0) || !(dT != 0)) {
+        delete h;
+        return fail(nullptr, TLBM_ERR_ARG, "relaxation time out of range (3 nu = %g, alpha = %g)", 3.0 * h->nu,
+                    h->alpha);
+    }
+    const double snu = 1.0 / (3.0 * h->nu + 0.5);
+    const double sq = 8.0 * (2.0 - snu) / (8.0 - snu);
+    const double s_rho = pick(prm.s_rho, 1.0), s_e = pick(prm.s_e, snu), s_eps = pick(prm.s_eps, snu);
+    const double s_j = pick(prm.s_j, 1.0), s_q = pick(prm.s_q, sq), s_pi = pick(prm.s_pi, snu);
+    const double s_m = pick(prm.s_m, sq);
+    if (dim == 2) {
+        const double S[9] = {s_rho, s_e, s_eps, s_j, s_q, s_j, s_q, snu, snu};
+        memcpy(h->S, S, sizeof(S));
+    } else {
+        const double S[19] = {s_rho, s_e, s_eps, s_j, s_q, s_j, s_q, s_j, s_q, snu,
+                              s_pi,  snu, s_pi,  snu, snu, snu, s_m, s_m, s_m};
+        memcpy(h->S, S, sizeof(S));
+    }
+    const double qj = 1.0 / (h->alpha / h->omega + 0.5);
+    const double qeven = 1.0 / (0.5 + 0.25 / (1.0 / qj - 0.5));
+    const double q_e = pick(prm.q_e, qeven), q_v = pick(prm.q_v, qeven);
+    if (dim == 2) {
+        const double Q[5] = {1.0, qj, qj, q_e, q_v};
+        memcpy(h->Q, Q, sizeof(Q));
+    } else {
+        const double Q[7] = {1.0, qj, qj, qj, q_e, q_v, q_v};
+        memcpy(h->Q, Q, sizeof(Q));
+    }
+
+    // device layout
+    KParams& kp = h->kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.L.nx = nx; kp.L.ny = ny; kp.L.nz = nz; kp.L.dim = dim;
+    kp.L.zg = dim == 3 ? 1 : 0;
+    kp.L.P = (int)align_up((size_t)nx + 16, ROW_ALIGN);
+    const long long rows = (long long)(ny + 2) * (dim == 3 ? nz + 2 : 1);
+    kp.L.plane = (long long)align_up((size_t)(SLOT_OFF + rows * kp.L.P + TAIL), 64);
+    kp.periodic = prm.periodic_mask;
+    kp.grav_axis = dim - 1;
+    kp.heat_axis = prm.walls == TLBM_RB ? dim - 1 : 0;
+    const int vec = step_vec(dim, precision);
+    kp.xmax_load = kp.L.P - vec;
+    kp.gbeta = h->gbeta; kp.omega = h->omega; kp.Th = h->prm.Th; kp.Tc = h->prm.Tc; kp.a_T = h->a_T;
+    for (int a = 0; a < 3; ++a) {
+        kp.body[a] = prm.body_force[a];
+        kp.bodyf[a] = (float)prm.body_force[a];
+    }
+    for (int k = 0; k < MAXQ; ++k) {
+        const double s = k < h->qf ? h->S[k] : 0.0;
+        kp.S[k] = s;
+        kp.Sh[k] = 1.0 - 0.5 * s;
+        kp.Sf[k] = (float)s;
+        kp.Shf[k] = (float)(1.0 - 0.5 * s);
+    }
+    for (int k = 0; k < 7; ++k) {
+        const double q = k < h->qg ? h->Q[k] : 0.0;
+        kp.Q[k] = q;
+        kp.Qf[k] = (float)q;
+    }
+    kp.gbetaf = (float)h->gbeta; kp.omegaf = (float)h->omega; kp.Thf = (float)h->prm.Th;
+    kp.Tcf = (float)h->prm.Tc; kp.a_Tf = (float)h->a_T;
+    double scale = pick(prm.store_scale, precision == TLBM_FP16_OFFSET ? 1024.0 : 1.0);
+    if (precision <= TLBM_FP32) scale = 1.0;
+    int scale_exp = 0;
+    if (!(scale > 0) || std::frexp(scale, &scale_exp) != 0.5) {
+        delete h;
+        return fail(nullptr, TLBM_ERR_ARG, "store_scale must be a power of two");
+    }
+    kp.scale = (float)scale;
+    kp.inv_scale = (float)(1.0 / scale);
+
+    h->elem = precision == TLBM_FP64 ? 8 : (precision == TLBM_FP32 ? 4 : 2);
+    h->popset_bytes = align_up((size_t)(h->qf + h->qg) * (size_t)kp.L.plane * h->elem, 256);
+    h->red_off = 2 * h->popset_bytes;
+    h->res_off = h->red_off + align_up((size_t)RED_BLOCKS * RED_FIELDS * sizeof(double), 256);
+    h->stage_off = h->res_off + 256;
+    const long long N = (long long)nx * ny * nz;
+    h->total_bytes = h->stage_off + align_up((size_t)std::min<long long>(N, STAGE_NODES) * sizeof(double), 256);
+    h->stream = nullptr;
+    h->cur = 0;
+    h->t = 0;
+    *out = h;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_required_bytes(tlbm_t h, size_t* bytes) {
+    TLBM_CHECK_HANDLE(h);
+    if (!bytes) return fail(h, TLBM_ERR_ARG, "bytes is NULL");
+    *bytes = h->total_bytes;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes) {
+    TLBM_CHECK_HANDLE(h);
+    if (!dev_ptr) return fail(h, TLBM_ERR_ARG, "dev_ptr is NULL");
+    if (((uintptr_t)dev_ptr) % 256) return fail(h, TLBM_ERR_ARG, "dev_ptr must be 256-byte aligned");
+    if (bytes < h->total_bytes)
+        return fail(h, TLBM_ERR_OOM, "bound block has %zu bytes, %zu needed", bytes, h->total_bytes);
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, dev_ptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaPointerGetAttributes");
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(h, TLBM_ERR_ARG, "dev_ptr is not device memory");
+    h->mem = (char*)dev_ptr;
+    h->mem_bytes = bytes;
+    h->buf[0] = h->mem;
+    h->buf[1] = h->mem + h->popset_bytes;
+    h->cur = 0;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_set_stream(tlbm_t h, void* s) {
+    TLBM_CHECK_HANDLE(h);
+    h->stream = (cudaStream_t)s;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (!std::isfinite(noise_amp) || noise_amp < 0) return fail(h, TLBM_ERR_ARG, "noise_amp must be finite, >= 0");
+    cudaError_t e = cudaMemsetAsync(h->mem, 0, 2 * h->popset_bytes, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    h->cur = 0;
+    e = with_types(h->dim, h->prec, [&](auto K) { return decltype(K)::init(h->buf[0], h->kp, seed, noise_amp, h->stream); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+    h->launches += 1;
+    h->t = 0;
+    return TLBM_OK;
+}
+
+static cudaError_t launch_one_step(tlbm_t h) {
+    const KParams& kp = h->kp;
+    const int vec = step_vec(h->dim, h->prec);
+    const int bx = 128;
+    const int threads_x = (h->nx + vec - 1) / vec;
+    dim3 block(bx, 1, 1);
+    dim3 grid((threads_x + bx - 1) / bx, h->ny, h->dim == 3 ? h->nz : 1);
+    const void* src = h->buf[h->cur];
+    void* dst = h->buf[h->cur ^ 1];
+    cudaError_t e;
+    if (h->prec == TLBM_FP64) e = launch_step_fp64(h->dim, src, dst, kp, grid, block, h->stream);
+    else if (h->dim == 2) e = launch_step_2d(h->prec, src, dst, kp, grid, block, h->stream);
+    else e = launch_step_3d(h->prec, src, dst, kp, grid, block, h->stream);
+    if (e == cudaSuccess) {
+        h->cur ^= 1;
+        h->t += 1;
+        h->launches += 1;
+    }
+    return e;
+}
+
+extern "C" int tlbm_step(tlbm_t h, int64_t n) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (n < 0) return fail(h, TLBM_ERR_ARG, "n must be >= 0");
+    for (int64_t i = 0; i < n; ++i) {
+        cudaError_t e = launch_one_step(h);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    }
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_macros(tlbm_t h, void* rho, void* ux, void* uy, void* uz, void* T, int out_dtype) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (out_dtype != TLBM_OUT_F64 && out_dtype != TLBM_OUT_F32) return fail(h, TLBM_ERR_ARG, "bad out_dtype");
+    if (h->dim == 2) uz = nullptr;
+    cudaError_t e = with_types(h->dim, h->prec, [&](auto K) {
+        return decltype(K)::macros(h->buf[h->cur], h->kp, rho, ux, uy, uz, T, out_dtype, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "macros kernel");
+    h->launches += 1;
+    return TLBM_OK;
+}
+
+// runs the two-pass reduction and copies the six results to the host
+static int run_reduce(tlbm_t h, double* res) {
+    double* partials = (double*)(h->mem + h->red_off);
+    double* out = (double*)(h->mem + h->res_off);
+    cudaError_t e = with_types(h->dim, h->prec, [&](auto K) {
+        return decltype(K)::reduce(h->buf[h->cur], h->kp, partials, out, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction kernel");
+    h->launches += 2;
+    e = cudaMemcpyAsync(res, out, RED_FIELDS * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_nusselt(tlbm_t h, double* nu) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (!nu) return fail(h, TLBM_ERR_ARG, "nu is NULL");
+    double r[RED_FIELDS];
+    int rc = run_reduce(h, r);
+    if (rc) return rc;
+    const double N = (double)h->nx * h->ny * h->nz;
+    const int ax = h->kp.heat_axis;
+    const double L = ax == 0 ? h->nx : (ax == 1 ? h->ny : h->nz);
+    *nu = 1.0 + L * (r[0] / N) / (h->alpha * (h->prm.Th - h->prm.Tc));
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_energy(tlbm_t h, double* ekin, double* mass) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    double r[RED_FIELDS];
+    int rc = run_reduce(h, r);
+    if (rc) return rc;
+    if (ekin) *ekin = r[1];
+    if (mass) *mass = r[2];
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_status(tlbm_t h, int* diverged, int64_t* step) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    double r[RED_FIELDS];
+    int rc = run_reduce(h, r);
+    if (rc) return rc;
+    if (diverged) *diverged = (r[4] != 0.0 || !(r[3] <= 0.25)) ? 1 : 0;
+    if (step) *step = h->t;
+    return TLBM_OK;
+}
+
+static int get_window(tlbm_t h, const Window& w, double* host_f, double* host_g) {
+    const long long N = (long long)w.wx * w.wy * w.wz;
+    double* stage = (double*)(h->mem + h->stage_off);
+    for (int pop = 0; pop < h->qf + h->qg; ++pop) {
+        double* dst = pop < h->qf ? (host_f ? host_f + (long long)pop * N : nullptr)
+                                  : (host_g ? host_g + (long long)(pop - h->qf) * N : nullptr);
+        if (!dst) continue;
+        for (long long n0 = 0; n0 < N; n0 += STAGE_NODES) {
+            const long long cnt = std::min(STAGE_NODES, N - n0);
+            cudaError_t e = with_types(h->dim, h->prec, [&](auto K) {
+                return decltype(K)::gather(h->buf[h->cur], stage, pop, n0, cnt, w, h->kp, h->stream);
+            });
+            if (e != cudaSuccess) return cuda_fail(h, e, "gather kernel");
+            h->launches += 1;
+            e = cudaMemcpyAsync(dst + n0, stage, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync D2H");
+            e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+        }
+    }
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_get_populations(tlbm_t h, double* host_f, double* host_g) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    const Window w = {0, 0, 0, h->nx, h->ny, h->nz};
+    return get_window(h, w, host_f, host_g);
+}
+
+extern "C" int tlbm_get_populations_window(tlbm_t h, int x0, int y0, int z0, int wx, int wy, int wz,
+                                           double* host_f, double* host_g) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (h->dim == 2) {
+        z0 = 0;
+        wz = 1;
+    }
+    if (x0 < 0 || y0 < 0 || z0 < 0 || wx < 1 || wy < 1 || wz < 1 || x0 + wx > h->nx || y0 + wy > h->ny ||
+        z0 + wz > h->nz)
+        return fail(h, TLBM_ERR_ARG, "window out of the cell");
+    const Window w = {x0, y0, z0, wx, wy, wz};
+    return get_window(h, w, host_f, host_g);
+}
+
+extern "C" int tlbm_set_populations(tlbm_t h, const double* host_f, const double* host_g) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (!host_f || !host_g) return fail(h, TLBM_ERR_ARG, "host_f and host_g are required");
+    const long long N = (long long)h->nx * h->ny * h->nz;
+    const Window full = {0, 0, 0, h->nx, h->ny, h->nz};
+    double* stage = (double*)(h->mem + h->stage_off);
+    cudaError_t e = cudaMemsetAsync(h->mem, 0, 2 * h->popset_bytes, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    h->cur = 0;
+    for (int pop = 0; pop < h->qf + h->qg; ++pop) {
+        const double* srcp = pop < h->qf ? host_f + (long long)pop * N : host_g + (long long)(pop - h->qf) * N;
+        for (long long n0 = 0; n0 < N; n0 += STAGE_NODES) {
+            const long long cnt = std::min(STAGE_NODES, N - n0);
+            e = cudaMemcpyAsync(stage, srcp + n0, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync H2D");
+            e = with_types(h->dim, h->prec, [&](auto K) {
+                return decltype(K)::scatter(h->buf[0], stage, pop, n0, cnt, full, h->kp, h->stream);
+            });
+            if (e != cudaSuccess) return cuda_fail(h, e, "scatter kernel");
+            h->launches += 1;
+        }
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    h->t = 0;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_derived(tlbm_t h, double* out, int cap, int* count) {
+    TLBM_CHECK_HANDLE(h);
+    if (!out && cap > 0) return fail(h, TLBM_ERR_ARG, "out is NULL");
+    double v[7 + MAXQ + 7];
+    int n = 0;
+    v[n++] = h->U; v[n++] = h->H; v[n++] = h->nu; v[n++] = h->alpha;
+    v[n++] = h->gbeta; v[n++] = h->a_T; v[n++] = h->omega;
+    for (int k = 0; k < h->qf; ++k) v[n++] = h->S[k];
+    for (int k = 0; k < h->qg; ++k) v[n++] = h->Q[k];
+    for (int i = 0; i < n && i < cap; ++i) out[i] = v[i];
+    if (count) *count = n < cap ? n : cap;
+    return TLBM_OK;
+}
+
+extern "C" const char* tlbm_last_error(tlbm_t h) { return h ? h->err : g_create_error; }
+
+extern "C" int tlbm_launch_count(tlbm_t h, int64_t* count) {
+    TLBM_CHECK_HANDLE(h);
+    if (!count) return fail(h, TLBM_ERR_ARG, "count is NULL");
+    *count = h->launches;
+    return TLBM_OK;
+}
+
+extern "C" void tlbm_destroy(tlbm_t h) { delete h; }

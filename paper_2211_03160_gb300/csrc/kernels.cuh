@@ -1,0 +1,581 @@
+// Fused stream + collide kernels of the DDF thermal lattice Boltzmann step
+// (Xu & Li, §2.2 Eqs. (5)-(7), split form Eqs. (10)-(11), fused here).
+//
+// Data layout ("pull buffer with a ghost halo").  Each population i of a set
+// lives in its own plane (SoA, x fastest, §3.1).  A plane has one ghost layer
+// around the cell: slots x in [-1, nx], y in [-1, ny] (and z in [-1, nz] in 3D),
+//     slot(x, y, z) = OFF + ((z + zg) * (ny + 2) + (y + 1)) * P + x,
+// zg = 1 in 3D and 0 in 2D, P = row pitch (multiple of 32, >= nx + 16).
+// Slot (s, i) holds the value that node s + e_i pulls as its pre-collision
+// f_i.  So a time step is a pure pull, f_i(x) = slot(x - e_i, i), with no
+// branch, and the wall rules are applied when the post-collision values are
+// written: a value leaving the cell through a wall (half-way bounce-back,
+// anti-bounce-back, adiabatic bounce-back, §2.2) is written into the ghost slot
+// that its own node will pull from in the next step; a value leaving through a
+// periodic face is written into the ghost slot its periodic image pulls from.
+// Every ghost slot that is ever read has exactly one writer.
+//
+// Precision variants: storage S in {double, float, __half, __nv_bfloat16};
+// collision in C = double for double storage, float otherwise.  The collision
+// works on deviations d_i = f_i - w_i; FP16/BF16 storage keeps d_i * scale
+// (flow) and g_i * scale (temperature), the "offset" storage.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lattice.cuh"
+
+namespace tlbm {
+
+constexpr int MAXQ = 19;
+constexpr int ROW_ALIGN = 32;   // row pitch multiple (elements)
+constexpr int SLOT_OFF = 64;    // offset of slot (0, -1[, -1]) row start (elements)
+constexpr int TAIL = 64;        // padding after the last row of a plane (elements)
+
+struct Layout {
+    int nx, ny, nz;          // nz = 1 in 2D
+    int dim;
+    int P;                   // row pitch in elements
+    int zg;                  // 1 in 3D, 0 in 2D
+    long long plane;         // elements per population plane (padded)
+    __host__ __device__ __forceinline__ long long row(int y, int z) const {
+        return (long long)SLOT_OFF + ((long long)(z + zg) * (ny + 2) + (y + 1)) * P;
+    }
+    __host__ __device__ __forceinline__ long long slot(int x, int y, int z) const {
+        return row(y, z) + x;
+    }
+};
+
+// Kernel parameters (passed by value).
+struct KParams {
+    Layout L;
+    int periodic;            // bit0 x, bit1 y, bit2 z
+    int heat_axis;           // axis normal to the isothermal walls
+    int grav_axis;           // 1 (2D) or 2 (3D)
+    int xmax_load;           // largest safe vector start for lanes past the row end
+    double gbeta, omega, Th, Tc, a_T;
+    double body[3];
+    double S[MAXQ], Sh[MAXQ];  // flow rates and 1 - S/2
+    double Q[7];
+    float Sf[MAXQ], Shf[MAXQ], Qf[7];
+    float gbetaf, omegaf, Thf, Tcf, a_Tf, bodyf[3];
+    float scale, inv_scale;  // offset-storage scale
+};
+
+// ------------------------------------------------------------------ storage
+
+template <class S>
+struct Storage;
+template <>
+struct Storage<double> {
+    using C = double;
+    static constexpr bool offset = false;
+};
+template <>
+struct Storage<float> {
+    using C = float;
+    static constexpr bool offset = false;
+};
+template <>
+struct Storage<__half> {
+    using C = float;
+    static constexpr bool offset = true;
+};
+template <>
+struct Storage<__nv_bfloat16> {
+    using C = float;
+    static constexpr bool offset = true;
+};
+
+template <class C, class S>
+__device__ __forceinline__ C to_c(S s) {
+    if constexpr (std::is_same<S, __half>::value) return __half2float(s);
+    else if constexpr (std::is_same<S, __nv_bfloat16>::value) return __bfloat162float(s);
+    else return C(s);
+}
+template <class S, class C>
+__device__ __forceinline__ S from_c(C c) {
+    if constexpr (std::is_same<S, __half>::value) return __float2half_rn(c);
+    else if constexpr (std::is_same<S, __nv_bfloat16>::value) return __float2bfloat16_rn(c);
+    else return S(c);
+}
+
+// parameter accessors in the compute precision
+template <class C> struct PV;
+template <> struct PV<double> {
+    __device__ static double S(const KParams& p, int k) { return p.S[k]; }
+    __device__ static double Sh(const KParams& p, int k) { return p.Sh[k]; }
+    __device__ static double Q(const KParams& p, int k) { return p.Q[k]; }
+    __device__ static double gbeta(const KParams& p) { return p.gbeta; }
+    __device__ static double omega(const KParams& p) { return p.omega; }
+    __device__ static double Th(const KParams& p) { return p.Th; }
+    __device__ static double Tc(const KParams& p) { return p.Tc; }
+    __device__ static double aT(const KParams& p) { return p.a_T; }
+    __device__ static double body(const KParams& p, int a) { return p.body[a]; }
+};
+template <> struct PV<float> {
+    __device__ static float S(const KParams& p, int k) { return p.Sf[k]; }
+    __device__ static float Sh(const KParams& p, int k) { return p.Shf[k]; }
+    __device__ static float Q(const KParams& p, int k) { return p.Qf[k]; }
+    __device__ static float gbeta(const KParams& p) { return p.gbetaf; }
+    __device__ static float omega(const KParams& p) { return p.omegaf; }
+    __device__ static float Th(const KParams& p) { return p.Thf; }
+    __device__ static float Tc(const KParams& p) { return p.Tcf; }
+    __device__ static float aT(const KParams& p) { return p.a_Tf; }
+    __device__ static float body(const KParams& p, int a) { return p.bodyf[a]; }
+};
+
+// flow weight w_i in precision C
+template <class L, class C>
+__device__ __forceinline__ constexpr C weight(int i) {
+    return C(L::w36(i)) / C(36);
+}
+
+// decode a stored flow value into its deviation d_i = f_i - w_i
+template <class LF, class S, class C>
+__device__ __forceinline__ C dec_f(S s, int i, C inv_scale) {
+    if constexpr (Storage<S>::offset) return to_c<C>(s) * inv_scale;
+    else return to_c<C>(s) - weight<LF, C>(i);
+}
+template <class LF, class S, class C>
+__device__ __forceinline__ S enc_f(C d, int i, C scale) {
+    if constexpr (Storage<S>::offset) return from_c<S>(d * scale);
+    else return from_c<S>(weight<LF, C>(i) + d);
+}
+template <class S, class C>
+__device__ __forceinline__ C dec_g(S s, C inv_scale) {
+    if constexpr (Storage<S>::offset) return to_c<C>(s) * inv_scale;
+    else return to_c<C>(s);
+}
+template <class S, class C>
+__device__ __forceinline__ S enc_g(C g, C scale) {
+    if constexpr (Storage<S>::offset) return from_c<S>(g * scale);
+    else return from_c<S>(g);
+}
+
+template <class C> struct ScaleOf;
+template <> struct ScaleOf<float> {
+    __device__ static float s(const KParams& p) { return p.scale; }
+    __device__ static float inv(const KParams& p) { return p.inv_scale; }
+};
+template <> struct ScaleOf<double> {
+    __device__ static double s(const KParams& p) { return (double)p.scale; }
+    __device__ static double inv(const KParams& p) { return (double)p.inv_scale; }
+};
+
+// ------------------------------------------------------------------ collision
+
+// Macroscopic moments of one node from deviations (§2.2):
+// rho = 1 + sum d, T = sum g, F = rho (g beta T ghat + a), u = (sum e f + F/2)/rho.
+// 2D flow MRT + Guo forcing (Eq. (5), Eq. (6a)) and D2Q5 thermal MRT (Eq. (7)),
+// in deviation form: every moment is taken relative to the rest state
+// (rho = 1, u = 0), m_w = M w = [1, -2, 1, 0, ...].
+template <class C>
+__device__ __forceinline__ void collide_2d(C (&d)[9], C (&g)[5], const KParams& p) {
+    using P = PV<C>;
+    C m[9], n[5];
+    moments<D2Q9>(d, m);
+    moments<D2Q5>(g, n);
+    const C drho = m[0];
+    const C rho = C(1) + drho;
+    const C T = n[0];
+    const C Fx = rho * P::body(p, 0);
+    const C Fy = rho * (P::gbeta(p) * T + P::body(p, 1));
+    const C ir = C(1) / rho;
+    const C ux = (m[3] + C(0.5) * Fx) * ir;
+    const C uy = (m[5] + C(0.5) * Fy) * ir;
+    const C ru2 = rho * (ux * ux + uy * uy);
+    // m_eq - m_w (Lallemand & Luo basis)
+    const C meq[9] = {drho,
+                      C(-2) * drho + C(3) * ru2,
+                      drho - C(3) * ru2,
+                      rho * ux,
+                      -rho * ux,
+                      rho * uy,
+                      -rho * uy,
+                      rho * (ux * ux - uy * uy),
+                      rho * ux * uy};
+    // M Ftilde, Eq. (6a) (last entry read as u Fy + v Fx)
+    const C uF = ux * Fx + uy * Fy;
+    const C mF[9] = {C(0),     C(6) * uF, C(-6) * uF, Fx, -Fx, Fy, -Fy,
+                     C(2) * (ux * Fx - uy * Fy), ux * Fy + uy * Fx};
+    static_for<9>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        m[k] = m[k] - P::S(p, k) * (m[k] - meq[k]) + P::Sh(p, k) * mF[k];
+    });
+    populations<D2Q9>(m, d);
+    // thermal: n_eq = [T, uT, vT, a_T T, 0]
+    const C neq[5] = {T, ux * T, uy * T, P::aT(p) * T, C(0)};
+    static_for<5>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        if constexpr (k > 0) n[k] = n[k] - P::Q(p, k) * (n[k] - neq[k]);
+    });
+    populations<D2Q5>(n, g);
+}
+
+// 3D: D3Q19 MRT (d'Humieres basis) + Guo forcing Eq. (6b), D3Q7 thermal MRT.
+// m_w = M w = [1, -11, 3, 0, ...].
+template <class C>
+__device__ __forceinline__ void collide_3d(C (&d)[19], C (&g)[7], const KParams& p) {
+    using P = PV<C>;
+    C m[19], n[7];
+    moments<D3Q19>(d, m);
+    moments<D3Q7>(g, n);
+    const C drho = m[0];
+    const C rho = C(1) + drho;
+    const C T = n[0];
+    const C Fx = rho * P::body(p, 0);
+    const C Fy = rho * P::body(p, 1);
+    const C Fz = rho * (P::gbeta(p) * T + P::body(p, 2));
+    const C ir = C(1) / rho;
+    const C ux = (m[3] + C(0.5) * Fx) * ir;
+    const C uy = (m[5] + C(0.5) * Fy) * ir;
+    const C uz = (m[7] + C(0.5) * Fz) * ir;
+    const C ru2 = rho * (ux * ux + uy * uy + uz * uz);
+    const C pxx = rho * (C(2) * ux * ux - uy * uy - uz * uz);
+    const C pww = rho * (uy * uy - uz * uz);
+    const C meq[19] = {drho,
+                       C(-11) * drho + C(19) * ru2,
+                       C(3) * drho - C(5.5) * ru2,
+                       rho * ux, C(-2) / C(3) * (rho * ux),
+                       rho * uy, C(-2) / C(3) * (rho * uy),
+                       rho * uz, C(-2) / C(3) * (rho * uz),
+                       pxx, C(-0.5) * pxx, pww, C(-0.5) * pww,
+                       rho * ux * uy, rho * uy * uz, rho * ux * uz,
+                       C(0), C(0), C(0)};
+    const C uF = ux * Fx + uy * Fy + uz * Fz;
+    const C mF[19] = {C(0), C(38) * uF, C(-11) * uF,
+                      Fx, C(-2) / C(3) * Fx, Fy, C(-2) / C(3) * Fy, Fz, C(-2) / C(3) * Fz,
+                      C(4) * ux * Fx - C(2) * uy * Fy - C(2) * uz * Fz,
+                      C(-2) * ux * Fx + uy * Fy + uz * Fz,
+                      C(2) * uy * Fy - C(2) * uz * Fz,
+                      -uy * Fy + uz * Fz,
+                      ux * Fy + uy * Fx, uy * Fz + uz * Fy, ux * Fz + uz * Fx,
+                      C(0), C(0), C(0)};
+    static_for<19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        m[k] = m[k] - P::S(p, k) * (m[k] - meq[k]) + P::Sh(p, k) * mF[k];
+    });
+    populations<D3Q19>(m, d);
+    const C neq[7] = {T, ux * T, uy * T, uz * T, P::aT(p) * T, C(0), C(0)};
+    static_for<7>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        if constexpr (k > 0) n[k] = n[k] - P::Q(p, k) * (n[k] - neq[k]);
+    });
+    populations<D3Q7>(n, g);
+}
+
+template <int DIM> struct Lat;
+template <> struct Lat<2> { using F = D2Q9; using G = D2Q5; };
+template <> struct Lat<3> { using F = D3Q19; using G = D3Q7; };
+
+template <int DIM, class C>
+__device__ __forceinline__ void collide(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q], const KParams& p) {
+    if constexpr (DIM == 2) collide_2d<C>(d, g, p);
+    else collide_3d<C>(d, g, p);
+}
+
+// Node macros from deviations (used by the diagnostic kernels).
+template <int DIM, class C>
+__device__ __forceinline__ void node_macros(const C (&d)[Lat<DIM>::F::Q], const C (&g)[Lat<DIM>::G::Q],
+                                            const KParams& p, C& rho, C (&u)[3], C& T) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    using P = PV<C>;
+    C drho = C(0), j[3] = {C(0), C(0), C(0)}, t = C(0);
+    static_for<LF::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        drho += d[i];
+        if constexpr (LF::e(i, 0) == 1) j[0] += d[i];
+        if constexpr (LF::e(i, 0) == -1) j[0] -= d[i];
+        if constexpr (LF::e(i, 1) == 1) j[1] += d[i];
+        if constexpr (LF::e(i, 1) == -1) j[1] -= d[i];
+        if constexpr (LF::e(i, 2) == 1) j[2] += d[i];
+        if constexpr (LF::e(i, 2) == -1) j[2] -= d[i];
+    });
+    static_for<LG::Q>([&](auto ii) { t += g[decltype(ii)::value]; });
+    rho = C(1) + drho;
+    T = t;
+    C F[3] = {rho * P::body(p, 0), rho * P::body(p, 1), rho * P::body(p, 2)};
+    F[DIM - 1] += rho * P::gbeta(p) * t;
+    const C ir = C(1) / rho;
+    u[0] = (j[0] + C(0.5) * F[0]) * ir;
+    u[1] = (j[1] + C(0.5) * F[1]) * ir;
+    u[2] = DIM == 3 ? (j[2] + C(0.5) * F[2]) * ir : C(0);
+}
+
+// ------------------------------------------------------------------ vector IO
+
+template <class S, int VEC>
+__device__ __forceinline__ void ld_vec(const S* __restrict__ p, S (&v)[VEC]) {
+    constexpr int B = VEC * (int)sizeof(S);
+    static_assert(B == 2 || B == 4 || B == 8 || B == 16, "vector width");
+    if constexpr (B == 16) {
+        uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+        memcpy(v, &t, 16);
+    } else if constexpr (B == 8) {
+        uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+        memcpy(v, &t, 8);
+    } else if constexpr (B == 4) {
+        unsigned int t = __ldg(reinterpret_cast<const unsigned int*>(p));
+        memcpy(v, &t, 4);
+    } else {
+        unsigned short t = __ldg(reinterpret_cast<const unsigned short*>(p));
+        memcpy(v, &t, 2);
+    }
+}
+
+template <class S, int VEC>
+__device__ __forceinline__ void st_vec(S* __restrict__ p, const S (&v)[VEC]) {
+    constexpr int B = VEC * (int)sizeof(S);
+    if constexpr (B == 16) {
+        uint4 t;
+        memcpy(&t, v, 16);
+        *reinterpret_cast<uint4*>(p) = t;
+    } else if constexpr (B == 8) {
+        uint2 t;
+        memcpy(&t, v, 8);
+        *reinterpret_cast<uint2*>(p) = t;
+    } else if constexpr (B == 4) {
+        unsigned int t;
+        memcpy(&t, v, 4);
+        *reinterpret_cast<unsigned int*>(p) = t;
+    } else {
+        unsigned short t;
+        memcpy(&t, v, 2);
+        *reinterpret_cast<unsigned short*>(p) = t;
+    }
+}
+
+// Load the VEC consecutive stored values that nodes x0 .. x0+VEC-1 pull in a
+// direction with x-component EX, from the source row `row` (slot index of x = 0
+// of the row y - e_y, z - e_z).  The aligned vector at x0 is loaded and shifted
+// by one element through a warp shuffle; the warp's edge lane fetches the one
+// element beyond its vector directly.  All 32 lanes must call this together.
+template <class S, int VEC, int EX, class C>
+__device__ __forceinline__ void pull_row(const S* __restrict__ plane, long long row, int x0ld, int lane,
+                                         C (&out)[VEC]) {
+    S v[VEC];
+    ld_vec<S, VEC>(plane + row + x0ld, v);
+    if constexpr (EX == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) out[k] = to_c<C>(v[k]);
+    } else if constexpr (EX == 1) {
+        // node x pulls from x - 1
+        C left = __shfl_up_sync(0xffffffffu, to_c<C>(v[VEC - 1]), 1);
+        if (lane == 0) left = to_c<C>(plane[row + x0ld - 1]);
+        out[0] = left;
+#pragma unroll
+        for (int k = 1; k < VEC; ++k) out[k] = to_c<C>(v[k - 1]);
+    } else {
+        // node x pulls from x + 1
+        C right = __shfl_down_sync(0xffffffffu, to_c<C>(v[0]), 1);
+        if (lane == 31) right = to_c<C>(plane[row + x0ld + VEC]);
+#pragma unroll
+        for (int k = 0; k < VEC - 1; ++k) out[k] = to_c<C>(v[k + 1]);
+        out[VEC - 1] = right;
+    }
+}
+
+// ------------------------------------------------------------------ wall rules
+
+// Write the post-collision value `val` of population i (set LS, flow or
+// thermal) of node (x, y, z) into the ghost slot that will pull it, if it
+// leaves the cell.  THERMAL selects the temperature rules of §2.2.
+template <class LS, bool THERMAL, int i, class S, class C>
+__device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams& p, int x, int y, int z, C val,
+                                            C scale) {
+    constexpr int ex = LS::e(i, 0), ey = LS::e(i, 1), ez = LS::e(i, 2);
+    if constexpr (ex == 0 && ey == 0 && ez == 0) return;
+    const Layout& L = p.L;
+    const int dx = x + ex, dy = y + ey, dz = z + ez;
+    const bool ox = dx < 0 || dx >= L.nx;
+    const bool oy = dy < 0 || dy >= L.ny;
+    const bool oz = (ez != 0) && (dz < 0 || dz >= L.nz);
+    if (!(ox || oy || oz)) return;
+    const bool wall = (ox && !(p.periodic & 1)) || (oy && !(p.periodic & 2)) || (oz && !(p.periodic & 4));
+    if (wall) {
+        // bounce-back into the node's own pull slot for the opposite direction
+        constexpr int o = LS::opp(i);
+        C out = val;
+        if constexpr (THERMAL) {
+            // axis-aligned: exactly one axis is crossed
+            const int ax = ox ? 0 : (oy ? 1 : 2);
+            if (ax == p.heat_axis) {
+                const bool hi = ox ? (dx >= L.nx) : (oy ? (dy >= L.ny) : (dz >= L.nz));
+                const C Tw = hi ? PV<C>::Tc(p) : PV<C>::Th(p);
+                out = -val + PV<C>::omega(p) * Tw;  // anti-bounce-back
+            }
+            base[(long long)o * L.plane + L.slot(dx, dy, dz)] = enc_g<S, C>(out, scale);
+        } else {
+            base[(long long)o * L.plane + L.slot(dx, dy, dz)] = enc_f<LS, S, C>(out, o, scale);
+        }
+    } else {
+        // periodic: the image node wrap(d) pulls from wrap(d) - e_i
+        const int wx = ox ? (dx < 0 ? dx + L.nx : dx - L.nx) : dx;
+        const int wy = oy ? (dy < 0 ? dy + L.ny : dy - L.ny) : dy;
+        const int wz = oz ? (dz < 0 ? dz + L.nz : dz - L.nz) : dz;
+        const long long s = L.slot(wx - ex, wy - ey, wz - ez);
+        if constexpr (THERMAL) base[(long long)i * L.plane + s] = enc_g<S, C>(val, scale);
+        else base[(long long)i * L.plane + s] = enc_f<LS, S, C>(val, i, scale);
+    }
+}
+
+// ------------------------------------------------------------------ step kernel
+
+// decode a raw stored value (already converted to C) into the flow deviation
+template <class LF, class S, class C>
+__device__ __forceinline__ C raw_to_dev(C raw, int i, C inv_scale) {
+    if constexpr (Storage<S>::offset) return raw * inv_scale;
+    else return raw - weight<LF, C>(i);
+}
+template <class S, class C>
+__device__ __forceinline__ C raw_to_g(C raw, C inv_scale) {
+    if constexpr (Storage<S>::offset) return raw * inv_scale;
+    else return raw;
+}
+
+// Pull the pre-collision populations of nodes x0 .. x0+VEC-1 of row (y, z):
+// f as deviations d_i = f_i - w_i, g as values.
+template <int DIM, class S, int VEC, class C>
+__device__ __forceinline__ void pull_node_vec(const S* __restrict__ src, const KParams& p, int y, int z, int x0ld,
+                                              int lane, C (&f)[Lat<DIM>::F::Q][VEC],
+                                              C (&g)[Lat<DIM>::G::Q][VEC]) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    const Layout& L = p.L;
+    const C inv_scale = ScaleOf<C>::inv(p);
+    const S* __restrict__ gsrc = src + (long long)LF::Q * L.plane;
+    static_for<LF::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        const long long row = L.row(y - LF::e(i, 1), z - LF::e(i, 2));
+        C t[VEC];
+        pull_row<S, VEC, LF::e(i, 0), C>(src + (long long)i * L.plane, row, x0ld, lane, t);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) f[i][k] = raw_to_dev<LF, S, C>(t[k], i, inv_scale);
+    });
+    static_for<LG::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        const long long row = L.row(y - LG::e(i, 1), z - LG::e(i, 2));
+        C t[VEC];
+        pull_row<S, VEC, LG::e(i, 0), C>(gsrc + (long long)i * L.plane, row, x0ld, lane, t);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g<S, C>(t[k], inv_scale);
+    });
+}
+
+// One thread updates VEC consecutive nodes of one row.  blockDim.x must be a
+// multiple of 32 so that a warp covers 32*VEC consecutive nodes of one row.
+template <int DIM, class S, int VEC>
+__global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    using C = typename Storage<S>::C;
+    constexpr int QF = LF::Q, QG = LG::Q;
+    const Layout& L = p.L;
+    const int lane = threadIdx.x & 31;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = DIM == 3 ? (int)blockIdx.z : 0;
+    if (y >= L.ny) return;  // uniform across the warp
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
+    const int x0ld = min(x0, p.xmax_load);
+    const C scale = ScaleOf<C>::s(p);
+
+    C f[QF][VEC], g[QG][VEC];
+    pull_node_vec<DIM, S, VEC, C>(src, p, y, z, x0ld, lane, f, g);
+
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        C fd[QF], gd[QG];
+#pragma unroll
+        for (int i = 0; i < QF; ++i) fd[i] = f[i][k];
+#pragma unroll
+        for (int i = 0; i < QG; ++i) gd[i] = g[i][k];
+        collide<DIM, C>(fd, gd, p);
+#pragma unroll
+        for (int i = 0; i < QF; ++i) f[i][k] = fd[i];
+#pragma unroll
+        for (int i = 0; i < QG; ++i) g[i][k] = gd[i];
+    }
+
+    if (x0 >= L.nx) return;
+    const long long own = L.row(y, z) + x0;
+    S* __restrict__ gdst = dst + (long long)QF * L.plane;
+    if (x0 + VEC <= L.nx) {
+        static_for<QF>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            S v[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v[k] = enc_f<LF, S, C>(f[i][k], i, scale);
+            st_vec<S, VEC>(dst + (long long)i * L.plane + own, v);
+        });
+        static_for<QG>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            S v[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v[k] = enc_g<S, C>(g[i][k], scale);
+            st_vec<S, VEC>(gdst + (long long)i * L.plane + own, v);
+        });
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            if (x0 + k < L.nx) {
+                static_for<QF>([&](auto ii) {
+                    constexpr int i = decltype(ii)::value;
+                    dst[(long long)i * L.plane + own + k] = enc_f<LF, S, C>(f[i][k], i, scale);
+                });
+                static_for<QG>([&](auto ii) {
+                    constexpr int i = decltype(ii)::value;
+                    gdst[(long long)i * L.plane + own + k] = enc_g<S, C>(g[i][k], scale);
+                });
+            }
+        }
+    }
+
+    // wall and periodic rules for values that leave the cell
+    const bool edge = (x0 == 0) || (x0 + VEC >= L.nx) || (y == 0) || (y == L.ny - 1) ||
+                      (DIM == 3 && (z == 0 || z == L.nz - 1));
+    if (edge) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            const int x = x0 + k;
+            if (x < L.nx) {
+                static_for<QF>([&](auto ii) {
+                    constexpr int i = decltype(ii)::value;
+                    ghost_write<LF, false, i, S, C>(dst, p, x, y, z, f[i][k], scale);
+                });
+                static_for<QG>([&](auto ii) {
+                    constexpr int i = decltype(ii)::value;
+                    ghost_write<LG, true, i, S, C>(gdst, p, x, y, z, g[i][k], scale);
+                });
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ diagnostics
+
+// Canonical pre-collision populations of one node (scalar pulls).
+template <int DIM, class S, class C>
+__device__ __forceinline__ void pull_node(const S* __restrict__ src, const KParams& p, int x, int y, int z,
+                                          C (&f)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q]) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    const Layout& L = p.L;
+    const C inv_scale = ScaleOf<C>::inv(p);
+    const S* __restrict__ gsrc = src + (long long)LF::Q * L.plane;
+    static_for<LF::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        const C raw = to_c<C>(src[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))]);
+        f[i] = raw_to_dev<LF, S, C>(raw, i, inv_scale);
+    });
+    static_for<LG::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        const C raw = to_c<C>(gsrc[(long long)i * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))]);
+        g[i] = raw_to_g<S, C>(raw, inv_scale);
+    });
+}
+
+}  // namespace tlbm

@@ -1,0 +1,328 @@
+"""Python binding of libtlbm.so (the C ABI in include/tlbm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch provides device memory and streams.  The functions keep the
+C names; `Sim` is a small convenience wrapper that owns a torch allocation for
+the bound device block.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+from . import build as _build
+
+TLBM_OK = 0
+TLBM_ERR_ARG = -1
+TLBM_ERR_OOM = -2
+TLBM_ERR_CUDA = -3
+TLBM_ERR_DIVERGED = -4
+TLBM_ERR_TIMEOUT = -5
+TLBM_ERR_UNBOUND = -6
+TLBM_ERR_UNSUPPORTED = -7
+
+TLBM_D2Q9_D2Q5 = 0
+TLBM_D3Q19_D3Q7 = 1
+TLBM_FP64, TLBM_FP32, TLBM_FP16_OFFSET, TLBM_BF16_OFFSET = 0, 1, 2, 3
+TLBM_RB, TLBM_SIDE_HEATED = 0, 1
+TLBM_OUT_F64, TLBM_OUT_F32 = 0, 1
+
+PRECISIONS = {"fp64": TLBM_FP64, "fp32": TLBM_FP32, "fp16": TLBM_FP16_OFFSET, "bf16": TLBM_BF16_OFFSET}
+
+
+class tlbm_params(C.Structure):
+    _fields_ = [
+        ("walls", C.c_int), ("periodic_mask", C.c_int), ("u_is_ma", C.c_int),
+        ("a_T", C.c_double), ("nu", C.c_double), ("alpha", C.c_double), ("gbeta", C.c_double),
+        ("s_rho", C.c_double), ("s_e", C.c_double), ("s_eps", C.c_double), ("s_j", C.c_double),
+        ("s_q", C.c_double), ("s_pi", C.c_double), ("s_m", C.c_double),
+        ("q_e", C.c_double), ("q_v", C.c_double),
+        ("body_force", C.c_double * 3), ("Th", C.c_double), ("Tc", C.c_double),
+        ("store_scale", C.c_double),
+    ]
+
+
+class tlbm_instance(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("Ra", C.c_double),
+                ("Pr", C.c_double), ("Ma", C.c_double), ("seed", C.c_uint64)]
+
+
+class TlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tlbm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "tlbm_default_params": (None, [C.POINTER(tlbm_params)]),
+    "tlbm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                              C.c_double, C.c_double, C.c_int, C.POINTER(tlbm_params)]),
+    "tlbm_required_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "tlbm_bind_memory": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "tlbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tlbm_init": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double]),
+    "tlbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "tlbm_macros": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "tlbm_nusselt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "tlbm_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "tlbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tlbm_set_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tlbm_get_populations_window": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                              C.c_void_p, C.c_void_p]),
+    "tlbm_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "tlbm_derived": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
+    "tlbm_last_error": (C.c_char_p, [C.c_void_p]),
+    "tlbm_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "tlbm_destroy": (None, [C.c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libtlbm.so (building it first if it is missing or stale).  Raises
+    if the library cannot be built or loaded: there is no fallback path."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libtlbm.so not found at {_build.LIB}; run the build first")
+            L = C.CDLL(_build.LIB)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(h, rc):
+    if rc != TLBM_OK:
+        msg = lib().tlbm_last_error(h)
+        raise TlbmError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ C names
+
+def tlbm_default_params(**overrides) -> tlbm_params:
+    p = tlbm_params()
+    lib().tlbm_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if k == "body_force":
+            for a in range(3):
+                p.body_force[a] = float(v[a])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def tlbm_create(nx, ny, nz, lattice, Ra, Pr, Ma, precision, params: tlbm_params | None = None):
+    h = C.c_void_p()
+    rc = lib().tlbm_create(C.byref(h), int(nx), int(ny), int(nz), int(lattice), float(Ra), float(Pr),
+                           float(Ma), int(precision), C.byref(params) if params is not None else None)
+    _check(None, rc)
+    return h
+
+
+def tlbm_required_bytes(h) -> int:
+    n = C.c_size_t()
+    _check(h, lib().tlbm_required_bytes(h, C.byref(n)))
+    return n.value
+
+
+def tlbm_bind_memory(h, dev_ptr: int, nbytes: int):
+    _check(h, lib().tlbm_bind_memory(h, C.c_void_p(dev_ptr), nbytes))
+
+
+def tlbm_set_stream(h, stream_handle: int):
+    _check(h, lib().tlbm_set_stream(h, C.c_void_p(stream_handle)))
+
+
+def tlbm_init(h, seed: int, noise_amp: float):
+    _check(h, lib().tlbm_init(h, C.c_uint64(seed), float(noise_amp)))
+
+
+def tlbm_step(h, n: int):
+    _check(h, lib().tlbm_step(h, C.c_int64(n)))
+
+
+def tlbm_macros(h, rho=None, ux=None, uy=None, uz=None, T=None, out_dtype=TLBM_OUT_F64):
+    _check(h, lib().tlbm_macros(h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T), int(out_dtype)))
+
+
+def tlbm_nusselt(h) -> float:
+    v = C.c_double()
+    _check(h, lib().tlbm_nusselt(h, C.byref(v)))
+    return v.value
+
+
+def tlbm_energy(h):
+    e, m = C.c_double(), C.c_double()
+    _check(h, lib().tlbm_energy(h, C.byref(e), C.byref(m)))
+    return e.value, m.value
+
+
+def tlbm_get_populations(h, host_f, host_g):
+    """host_f, host_g: C-contiguous float64 numpy arrays (or None)."""
+    fp = None if host_f is None else C.c_void_p(host_f.ctypes.data)
+    gp = None if host_g is None else C.c_void_p(host_g.ctypes.data)
+    _check(h, lib().tlbm_get_populations(h, fp, gp))
+
+
+def tlbm_get_populations_window(h, x0, y0, z0, wx, wy, wz, host_f, host_g):
+    fp = None if host_f is None else C.c_void_p(host_f.ctypes.data)
+    gp = None if host_g is None else C.c_void_p(host_g.ctypes.data)
+    _check(h, lib().tlbm_get_populations_window(h, x0, y0, z0, wx, wy, wz, fp, gp))
+
+
+def tlbm_set_populations(h, host_f, host_g):
+    _check(h, lib().tlbm_set_populations(h, C.c_void_p(host_f.ctypes.data), C.c_void_p(host_g.ctypes.data)))
+
+
+def tlbm_status(h):
+    d, s = C.c_int(), C.c_int64()
+    _check(h, lib().tlbm_status(h, C.byref(d), C.byref(s)))
+    return bool(d.value), s.value
+
+
+def tlbm_derived(h) -> list:
+    buf = (C.c_double * 64)()
+    n = C.c_int()
+    _check(h, lib().tlbm_derived(h, buf, 64, C.byref(n)))
+    return list(buf[: n.value])
+
+
+def tlbm_last_error(h) -> str:
+    m = lib().tlbm_last_error(h)
+    return m.decode() if m else ""
+
+
+def tlbm_launch_count(h) -> int:
+    n = C.c_int64()
+    _check(h, lib().tlbm_launch_count(h, C.byref(n)))
+    return n.value
+
+
+def tlbm_destroy(h):
+    if h:
+        lib().tlbm_destroy(h)
+
+
+# ------------------------------------------------------------------ convenience
+
+class Sim:
+    """One cell on the current CUDA device; device memory is a torch uint8
+    tensor bound to the handle."""
+
+    def __init__(self, nx, ny, nz=1, lattice=TLBM_D2Q9_D2Q5, Ra=1e5, Pr=0.71, Ma=0.1, precision=TLBM_FP32,
+                 stream=None, **params):
+        import torch
+
+        self.lattice = lattice
+        self.nx, self.ny = nx, ny
+        self.nz = nz if lattice == TLBM_D3Q19_D3Q7 else 1
+        self.qf = 9 if lattice == TLBM_D2Q9_D2Q5 else 19
+        self.qg = 5 if lattice == TLBM_D2Q9_D2Q5 else 7
+        self.N = self.nx * self.ny * self.nz
+        self.precision = precision
+        self.params = tlbm_default_params(**params)
+        self.h = tlbm_create(nx, ny, self.nz, lattice, Ra, Pr, Ma, precision, self.params)
+        self.nbytes = tlbm_required_bytes(self.h)
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        tlbm_bind_memory(self.h, self.mem.data_ptr(), self.nbytes)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        tlbm_set_stream(self.h, s.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            tlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx) if self.lattice == TLBM_D3Q19_D3Q7 else (self.ny, self.nx)
+
+    def init(self, seed, noise_amp):
+        tlbm_init(self.h, seed, noise_amp)
+
+    def step(self, n=1):
+        tlbm_step(self.h, n)
+
+    def macros(self, dtype=None) -> dict:
+        import torch
+
+        dtype = dtype or torch.float64
+        out = {k: torch.empty(self.shape, dtype=dtype, device="cuda") for k in ("rho", "ux", "uy", "uz", "T")}
+        tlbm_macros(self.h, out["rho"], out["ux"], out["uy"], out["uz"] if self.lattice else None, out["T"],
+                    TLBM_OUT_F64 if dtype == torch.float64 else TLBM_OUT_F32)
+        if not self.lattice:
+            out["uz"].zero_()
+        return out
+
+    def nusselt(self):
+        return tlbm_nusselt(self.h)
+
+    def energy(self):
+        return tlbm_energy(self.h)
+
+    def status(self):
+        return tlbm_status(self.h)
+
+    def derived(self) -> dict:
+        v = tlbm_derived(self.h)
+        d = dict(U=v[0], H=v[1], nu=v[2], alpha=v[3], gbeta=v[4], a_T=v[5], omega=v[6])
+        d["S"] = v[7:7 + self.qf]
+        d["Q"] = v[7 + self.qf:7 + self.qf + self.qg]
+        return d
+
+    def get_populations(self):
+        import numpy as np
+
+        f = np.zeros((self.qf,) + self.shape)
+        g = np.zeros((self.qg,) + self.shape)
+        tlbm_get_populations(self.h, f, g)
+        return f, g
+
+    def get_window(self, x0, y0, z0, wx, wy, wz=1):
+        import numpy as np
+
+        shp = (wz, wy, wx) if self.lattice == TLBM_D3Q19_D3Q7 else (wy, wx)
+        f = np.zeros((self.qf,) + shp)
+        g = np.zeros((self.qg,) + shp)
+        tlbm_get_populations_window(self.h, x0, y0, z0, wx, wy, wz, f, g)
+        return f, g
+
+    def set_populations(self, f, g):
+        import numpy as np
+
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.size == self.qf * self.N and g.size == self.qg * self.N
+        tlbm_set_populations(self.h, f, g)
+
+    @property
+    def launches(self):
+        return tlbm_launch_count(self.h)

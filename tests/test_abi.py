@@ -1,0 +1,129 @@
+"""C-ABI contract checks that need no GPU: the library loads, exports every
+function declared in include/tlbm.h, and validates host-side arguments."""
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"TLBM_API\s+[\w\s\*]+?\b(tlbm_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2211_03160_gb300 import tlbm
+    tlbm.lib()
+    return tlbm
+
+
+def test_library_exports_every_declared_symbol(T):
+    names = _declared("tlbm.h")
+    assert len(names) >= 18
+    out = subprocess.run(["nm", "-D", "--defined-only", T.library_path()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (tlbm_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = T.lib()
+    for n in names:
+        assert getattr(L, n) is not None
+
+
+def test_binding_has_every_c_name(T):
+    for n in _declared("tlbm.h"):
+        if n == "tlbm_default_params":
+            continue
+        assert hasattr(T, n), n
+
+
+def test_default_params_are_nan(T):
+    p = T.tlbm_default_params()
+    assert p.walls == T.TLBM_RB and p.periodic_mask == 0
+    for k in ("a_T", "nu", "alpha", "gbeta", "s_q", "q_e", "Th", "Tc", "store_scale"):
+        assert math.isnan(getattr(p, k))
+
+
+@pytest.mark.parametrize("args,code", [
+    ((2, 10, 1, 0, 1e5, 0.71, 0.1, 1), -1),
+    ((10, 2, 1, 0, 1e5, 0.71, 0.1, 1), -1),
+    ((10, 10, 2, 1, 1e5, 0.71, 0.1, 1), -1),
+    ((10, 10, 1, 0, 0.0, 0.71, 0.1, 1), -1),
+    ((10, 10, 1, 0, 1e5, -1.0, 0.1, 1), -1),
+    ((10, 10, 1, 0, 1e5, 0.71, 0.0, 1), -1),
+    ((10, 10, 1, 7, 1e5, 0.71, 0.1, 1), -1),
+    ((10, 10, 1, 0, 1e5, 0.71, 0.1, 9), -7),
+])
+def test_create_rejects_invalid(T, args, code):
+    with pytest.raises(T.TlbmError) as ei:
+        T.tlbm_create(*args)
+    assert ei.value.code == code
+    assert T.tlbm_last_error(None)
+
+
+def test_create_rejects_tiny_relaxation(T):
+    p = T.tlbm_default_params(nu=1e-8)
+    with pytest.raises(T.TlbmError):
+        T.tlbm_create(10, 10, 1, 0, 1e5, 0.71, 0.1, 1, p)
+
+
+def test_unbound_handle_refuses_work(T):
+    h = T.tlbm_create(33, 17, 1, 0, 1e5, 0.71, 0.1, 1)
+    try:
+        for fn in (lambda: T.tlbm_step(h, 1), lambda: T.tlbm_init(h, 1, 1e-3), T.tlbm_nusselt and
+                   (lambda: T.tlbm_nusselt(h))):
+            with pytest.raises(T.TlbmError) as ei:
+                fn()
+            assert ei.value.code == T.TLBM_ERR_UNBOUND
+        assert T.tlbm_required_bytes(h) > 0
+        assert T.tlbm_launch_count(h) == 0
+    finally:
+        T.tlbm_destroy(h)
+
+
+def test_required_bytes_cover_both_buffers(T):
+    for lattice, shape, prec, elem, q in ((0, (8193, 8193, 1), 1, 4, 14), (1, (385, 385, 385), 2, 2, 26),
+                                           (0, (129, 129, 1), 0, 8, 14)):
+        h = T.tlbm_create(*shape, lattice, 1e7, 0.71, 0.1, prec)
+        try:
+            n = T.tlbm_required_bytes(h)
+            nodes = shape[0] * shape[1] * shape[2]
+            assert n >= 2 * q * nodes * elem
+            assert n < 2 * q * nodes * elem * 1.25 + (64 << 20)
+            assert n % 256 == 0
+        finally:
+            T.tlbm_destroy(h)
+
+
+def test_derived_parameters_match_oracle(T, O):
+    """Both sides map (Ra, Pr, Ma) to the same lattice parameters and rates."""
+    for lattice, shape in ((0, (129, 129, 1)), (1, (17, 19, 23))):
+        h = T.tlbm_create(*shape, lattice, 1e5, 0.71, 0.1, 0)
+        try:
+            d = T.tlbm_derived(h)
+        finally:
+            T.tlbm_destroy(h)
+        o = O.Sim(*shape, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1).derived()
+        ref = [o["U"], o["H"], o["nu"], o["alpha"], o["gbeta"], o["a_T"], o["omega"], *o["S"], *o["Q"]]
+        assert len(d) == len(ref)
+        for a, b in zip(d, ref):
+            assert a == pytest.approx(b, rel=1e-15, abs=1e-300)
+
+
+def test_bind_rejects_null_and_small(T):
+    h = T.tlbm_create(33, 17, 1, 0, 1e5, 0.71, 0.1, 1)
+    try:
+        with pytest.raises(T.TlbmError) as ei:
+            T.tlbm_bind_memory(h, 0, 1 << 30)
+        assert ei.value.code == T.TLBM_ERR_ARG
+        with pytest.raises(T.TlbmError) as ei:
+            T.tlbm_bind_memory(h, 1 << 20, 16)
+        assert ei.value.code == T.TLBM_ERR_OOM
+    finally:
+        T.tlbm_destroy(h)

@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+Element-by-element comparisons on identical seeded inputs:
+  - FP64 storage: within 1e-12 max-abs per field (rho, u, T) after 1000 and
+    2000 steps on the 129^2 Rayleigh-Benard case at Ra = 1e5;
+  - every precision on tiny and ragged grids with random populations, every
+    wall / periodic combination, one and several steps (edge and corner rules);
+  - FP32 / FP16 / BF16 offset storage against FP64 within stated tolerances.
+"""
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+D2, D3 = 0, 1
+FP64, FP32, FP16, BF16 = 0, 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_03160_gb300 import tlbm
+
+    tlbm.lib()
+    return tlbm
+
+
+def _fields(sim):
+    return {k: v.cpu().numpy() for k, v in sim.macros().items()}
+
+
+def _maxerr(a, b, keys=("rho", "ux", "uy", "uz", "T")):
+    return {k: float(np.abs(a[k] - b[k]).max()) for k in keys}
+
+
+# ------------------------------------------------------------------ FP64 headline parity
+
+def test_fp64_2d_config1_1000_2000_steps(T, O):
+    """129^2, Ra = 1e5, Pr = 0.71, Ma = 0.1, RB walls, noise 1e-3, seed 1."""
+    g = T.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64)
+    o = O.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1)
+    g.init(1, 1e-3)
+    o.init(1, 1e-3)
+    e0 = _maxerr(_fields(g), o.macros())
+    assert max(e0.values()) < 1e-15, e0
+    for target in (1000, 2000):
+        g.step(target - o.time)
+        o.step(target - o.time)
+        e = _maxerr(_fields(g), o.macros())
+        assert max(e.values()) < 1e-12, (target, e)
+    assert abs(g.nusselt() - o.nusselt()) < 1e-10
+    eg, mg = g.energy()
+    eo, mo = o.energy()
+    assert abs(mg - mo) < 1e-9 and abs(eg - eo) < 1e-12 * max(1.0, eo)
+    fg, gg = g.get_populations()
+    fo, go = o.get_populations()
+    assert np.abs(fg - fo).max() < 1e-12 and np.abs(gg - go).max() < 1e-12
+
+
+def test_fp64_3d_parity(T, O):
+    """D3Q19 + D3Q7 cube, 500 steps (walls on every face)."""
+    n = 33
+    g = T.Sim(n, n, n, lattice=D3, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64)
+    o = O.Sim(n, n, n, lattice=D3, Ra=1e5, Pr=0.71, Ma=0.1)
+    O.set_threads(8)
+    g.init(3, 1e-3)
+    o.init(3, 1e-3)
+    g.step(500)
+    o.step(500)
+    e = _maxerr(_fields(g), o.macros())
+    assert max(e.values()) < 1e-12, e
+    assert abs(g.nusselt() - o.nusselt()) < 1e-10
+
+
+# ------------------------------------------------------------------ edge cases, every precision
+
+TOL1 = {FP64: 1e-14, FP32: 2e-6, FP16: 2e-3, BF16: 1.2e-2}
+
+EDGE_CASES = [
+    # lattice, (nx, ny, nz), walls, periodic mask
+    (D2, (3, 3, 1), 0, 0), (D2, (4, 5, 1), 1, 0), (D2, (5, 4, 1), 0, 1), (D2, (7, 6, 1), 0, 2),
+    (D2, (6, 3, 1), 1, 3), (D2, (37, 9, 1), 0, 0), (D2, (131, 5, 1), 0, 1), (D2, (257, 4, 1), 1, 0),
+    (D3, (5, 4, 3), 0, 0), (D3, (3, 4, 5), 1, 0), (D3, (4, 3, 3), 0, 1), (D3, (3, 3, 4), 0, 6),
+    (D3, (4, 3, 3), 1, 5), (D3, (35, 4, 3), 0, 0), (D3, (70, 3, 4), 0, 7),
+]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, FP16, BF16])
+@pytest.mark.parametrize("lattice,shape,walls,pm", EDGE_CASES)
+def test_one_step_random_populations(T, O, prec, lattice, shape, walls, pm):
+    """Random populations set through the ABI; one and three steps must match
+    the oracle started from the same values as the GPU stores them."""
+    nx, ny, nz = shape
+    kw = dict(walls=walls, periodic_mask=pm)
+    g = T.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec, **kw)
+    o = O.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1, **kw)
+    qf, qg = (9, 5) if lattice == D2 else (19, 7)
+    seed = 7 + 13 * lattice + 3 * walls + pm + 100 * prec + nx
+    f = inputs.uniform_array(seed, (qf,) + o.shape, 0.02, 0.2)
+    gg = inputs.uniform_array(seed + 1, (qg,) + o.shape, -0.1, 0.1)
+    g.set_populations(f, gg)
+    f0, g0 = g.get_populations()  # as stored in the GPU precision
+    o.set_populations(f0, g0)
+    for n in (1, 2):
+        g.step(n)
+        o.step(n)
+        fg, ggg = g.get_populations()
+        fo, go = o.get_populations()
+        ef = np.abs(fg - fo).max() / np.abs(fo).max()
+        eg = np.abs(ggg - go).max() / np.abs(go).max()
+        assert ef < TOL1[prec] * n and eg < TOL1[prec] * n, (n, ef, eg)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, FP16, BF16])
+@pytest.mark.parametrize("lattice,shape", [(D2, (129, 65, 1)), (D3, (37, 20, 18))])
+def test_init_matches_oracle(T, O, prec, lattice, shape):
+    """Same counter-based noise on both sides: the initial temperature agrees
+    to the storage precision, and exactly in FP64."""
+    g = T.Sim(*shape, lattice=lattice, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
+    o = O.Sim(*shape, lattice=lattice, Ra=1e6, Pr=0.71, Ma=0.1)
+    g.init(42, 1e-3)
+    o.init(42, 1e-3)
+    tg, to = _fields(g)["T"], o.macros()["T"]
+    tol = {FP64: 1e-16, FP32: 1e-7, FP16: 1e-3, BF16: 8e-3}[prec]
+    assert np.abs(tg - to).max() < tol
+
+
+# ------------------------------------------------------------------ reduced precision vs FP64
+
+@pytest.mark.parametrize("prec,tol_T,tol_u", [(FP32, 2e-5, 2e-3), (FP16, 3e-2, 0.25), (BF16, 0.1, 1.0)])
+def test_reduced_precision_fields_vs_oracle(T, O, prec, tol_T, tol_u):
+    """129^2, Ra = 1e5, 400 steps: field error max|a - b| / max|b| per field."""
+    g = T.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec)
+    o = O.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1)
+    g.init(1, 1e-3)
+    o.init(1, 1e-3)
+    g.step(400)
+    o.step(400)
+    a, b = _fields(g), o.macros()
+    rel = {k: float(np.abs(a[k] - b[k]).max() / np.abs(b[k]).max()) for k in ("T", "ux", "uy")}
+    print("field rel err", prec, rel)
+    assert rel["T"] < tol_T and rel["ux"] < tol_u and rel["uy"] < tol_u, rel
+
+
+# ------------------------------------------------------------------ bench-size sampled parity
+
+@pytest.mark.parametrize("prec,tol", [(FP32, 3e-6), (FP16, 3e-3)])
+def test_full_size_sampled_windows(T, O, prec, tol):
+    """8193^2 at Ra = 1e8 in the benchmark's launch configuration: after a few
+    steps, windows at a corner, a wall and the interior are read back; one
+    oracle step on each window (with the full cell's parameters) must match the
+    GPU's next state on the window's inner nodes."""
+    n = 8193
+    g = T.Sim(n, n, lattice=D2, Ra=1e8, Pr=0.71, Ma=0.1, precision=prec)
+    d = g.derived()
+    g.init(2, 1e-3)
+    g.step(5)
+    w = 24
+    boxes = [(0, 0), (n - w, n - w), (4000, 0), (0, 5000), (n - w, 3000), (4090, 4090), (8000, n - w)]
+    before = [g.get_window(x0, y0, 0, w, w) for x0, y0 in boxes]
+    g.step(1)
+    after = [g.get_window(x0, y0, 0, w, w) for x0, y0 in boxes]
+    for (x0, y0), (f0, g0), (f1, g1) in zip(boxes, before, after):
+        o = O.Sim(w, w, lattice=D2, Ra=1e8, Pr=0.71, Ma=0.1, nu=d["nu"], alpha=d["alpha"], gbeta=d["gbeta"])
+        o.set_populations(f0, g0)
+        o.step(1)
+        fo, go = o.get_populations()
+        # inner nodes: drop a side only where it is an artificial window edge
+        xs = slice(0 if x0 == 0 else 1, w if x0 + w == n else w - 1)
+        ys = slice(0 if y0 == 0 else 1, w if y0 + w == n else w - 1)
+        ef = np.abs(f1[:, ys, xs] - fo[:, ys, xs]).max() / np.abs(fo).max()
+        eg = np.abs(g1[:, ys, xs] - go[:, ys, xs]).max() / np.abs(go).max()
+        assert ef < tol and eg < tol, ((x0, y0), ef, eg)
+    div, step = g.status()
+    assert not div and step == 6
+
+
+def test_mass_conserved_on_gpu(T):
+    """FP64 storage: sum rho is constant to round-off over 1000 steps."""
+    g = T.Sim(257, 129, lattice=D2, Ra=1e6, Pr=0.71, Ma=0.1, precision=FP64)
+    g.init(5, 1e-3)
+    m0 = g.energy()[1]
+    g.step(1000)
+    m1 = g.energy()[1]
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+def test_reductions_are_deterministic(T):
+    g = T.Sim(513, 257, lattice=D2, Ra=1e7, Pr=0.71, Ma=0.1, precision=FP32)
+    g.init(9, 1e-3)
+    g.step(50)
+    a = [g.nusselt() for _ in range(3)]
+    assert a[0] == a[1] == a[2]
+
+
+def test_divergence_is_reported(T):
+    """A state with |u| > 0.5 is flagged by tlbm_status."""
+    g = T.Sim(16, 16, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64)
+    f = np.zeros((9, 16, 16))
+    gg = np.zeros((5, 16, 16))
+    f[0] = 0.5
+    f[1] = 0.5  # u_x = 0.5/1.0 at every node
+    g.set_populations(f, gg)
+    div, _ = g.status()
+    assert div
+    g.init(1, 1e-3)
+    assert not g.status()[0]
+
+
+def test_launch_count(T):
+    g = T.Sim(64, 64, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP32)
+    g.init(1, 0.0)
+    c0 = g.launches
+    g.step(10)
+    assert g.launches - c0 == 10
