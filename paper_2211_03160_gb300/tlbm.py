@@ -306,6 +306,10 @@ class Sim:
         tlbm_get_populations(self.h, f, g)
         return f, g
 
+    def get_populations_into(self, f, g):
+        """Fill preallocated C-contiguous float64 arrays (e.g. pinned host memory)."""
+        tlbm_get_populations(self.h, f, g)
+
     def get_window(self, x0, y0, z0, wx, wy, wz=1):
         import numpy as np
 

@@ -56,7 +56,7 @@ def test_fp64_2d_config1_1000_2000_steps(T, O):
     assert abs(g.nusselt() - o.nusselt()) < 1e-10
     eg, mg = g.energy()
     eo, mo = o.energy()
-    assert abs(mg - mo) < 1e-9 and abs(eg - eo) < 1e-12 * max(1.0, eo)
+    assert abs(mg - mo) / mo < 1e-12 and abs(eg - eo) < 1e-10 * eo
     fg, gg = g.get_populations()
     fo, go = o.get_populations()
     assert np.abs(fg - fo).max() < 1e-12 and np.abs(gg - go).max() < 1e-12
