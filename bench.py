@@ -42,8 +42,9 @@ METRIC = ("GLUPS & % HBM roofline, 8193² D2Q9+D2Q5 / 385³ D3Q19+D3Q7, "
 BYTES_PER_LU = {(2, "fp64"): 224, (2, "fp32"): 112, (2, "fp16"): 56, (2, "bf16"): 56,
                 (3, "fp64"): 416, (3, "fp32"): 208, (3, "fp16"): 104, (3, "bf16"): 104}
 KERNEL_SOURCES = ["paper_2211_03160_gb300/csrc/kernels.cuh", "paper_2211_03160_gb300/csrc/lattice.cuh",
-                  "paper_2211_03160_gb300/csrc/step_2d.cu", "paper_2211_03160_gb300/csrc/step_3d.cu",
-                  "paper_2211_03160_gb300/csrc/step_fp64.cu"]
+                  "paper_2211_03160_gb300/csrc/dispatch.h", "paper_2211_03160_gb300/csrc/step_2d_f32.cu",
+                  "paper_2211_03160_gb300/csrc/step_2d_f16.cu", "paper_2211_03160_gb300/csrc/step_3d_f32.cu",
+                  "paper_2211_03160_gb300/csrc/step_3d_f16.cu", "paper_2211_03160_gb300/csrc/step_fp64.cu"]
 
 
 def kernel_hash() -> str:

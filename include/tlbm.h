@@ -175,6 +175,16 @@ TLBM_API int tlbm_status(tlbm_t h, int* diverged, int64_t* step);
  * through *count. */
 TLBM_API int tlbm_derived(tlbm_t h, double* out, int cap, int* count);
 
+/* Choose the step kernel variant: vec = nodes per thread (0 = default),
+ * form = 0 automatic (two-relaxation-time evaluation when the rates allow it,
+ * else the general MRT), 1 general MRT, 2 two-relaxation-time (TLBM_ERR_ARG if
+ * the rates are not of that form); block_x (multiple of 32) x block_y threads
+ * per block (0 = default 128 x 1).  All variants compute the same collision;
+ * TLBM_ERR_UNSUPPORTED if the variant is not compiled. */
+TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y);
+/* Current variant (form reported as 1 MRT or 2 TRT).  Outputs may be NULL. */
+TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y);
+
 /* Text of the last error on this handle ("" if none); valid until the next call
  * on the handle.  A NULL handle returns the last error of a failed tlbm_create
  * in this thread. */

@@ -22,8 +22,10 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 # translation unit -> extra flags
 UNITS = {
     "api.cu": [],
-    "step_2d.cu": [],
-    "step_3d.cu": [],
+    "step_2d_f32.cu": [],
+    "step_2d_f16.cu": [],
+    "step_3d_f32.cu": [],
+    "step_3d_f16.cu": [],
     "step_fp64.cu": ["--fmad=false"],
 }
 

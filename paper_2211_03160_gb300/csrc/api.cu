@@ -36,6 +36,7 @@ struct tlbm_s {
     double U, H, nu, alpha, gbeta, a_T, omega;
     double S[MAXQ], Q[7];
     KParams kp;
+    int vec, trt, bx, by;      // step kernel variant and block shape
     size_t elem;               // bytes per stored value
     size_t popset_bytes;       // one population buffer (f planes then g planes)
     size_t red_off, res_off, stage_off, total_bytes;
@@ -375,6 +376,12 @@ extern "C" void tlbm_default_params(tlbm_params* p) {
 
 static double pick(double v, double d) { return std::isnan(v) ? d : v; }
 
+// nodes per thread of the step kernel unless tuned otherwise
+static int default_vec(int dim, int prec) {
+    if (dim == 2) return prec == TLBM_FP64 ? 2 : (prec == TLBM_FP32 ? 4 : 8);
+    return prec == TLBM_FP64 ? 1 : (prec == TLBM_FP32 ? 2 : 4);
+}
+
 extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, double Ra, double Pr, double Ma,
                            int precision, const tlbm_params* pin) {
     g_create_error[0] = 0;
@@ -459,8 +466,34 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
     kp.periodic = prm.periodic_mask;
     kp.grav_axis = dim - 1;
     kp.heat_axis = prm.walls == TLBM_RB ? dim - 1 : 0;
-    const int vec = step_vec(dim, precision);
-    kp.xmax_load = kp.L.P - vec;
+    // two-relaxation-time form applies when the even / odd non-conserved rates coincide
+    {
+        const int ev2[] = {1, 2, 7, 8}, od2[] = {4, 6};
+        const int ev3[] = {1, 2, 9, 10, 11, 12, 13, 14, 15}, od3[] = {4, 6, 8, 16, 17, 18};
+        const int* ev = dim == 2 ? ev2 : ev3;
+        const int* od = dim == 2 ? od2 : od3;
+        const int nev = dim == 2 ? 4 : 9, nod = dim == 2 ? 2 : 6;
+        bool ok = true;
+        for (int k = 1; k < nev; ++k) ok = ok && h->S[ev[k]] == h->S[ev[0]];
+        for (int k = 1; k < nod; ++k) ok = ok && h->S[od[k]] == h->S[od[0]];
+        const int tev = dim == 2 ? 3 : 4;  // first even non-conserved thermal moment
+        for (int k = tev + 1; k < h->qg; ++k) ok = ok && h->Q[k] == h->Q[tev];
+        for (int k = 2; k < tev; ++k) ok = ok && h->Q[k] == h->Q[1];
+        kp.trt = ok ? 1 : 0;
+        kp.sp = h->S[ev[0]];
+        kp.sm = h->S[od[0]];
+        kp.shp = 1.0 - 0.5 * kp.sp;
+        kp.shm = 1.0 - 0.5 * kp.sm;
+        kp.qp = h->Q[tev];
+        kp.qm = h->Q[1];
+        kp.spf = (float)kp.sp; kp.smf = (float)kp.sm; kp.shpf = (float)kp.shp; kp.shmf = (float)kp.shm;
+        kp.qpf = (float)kp.qp; kp.qmf = (float)kp.qm;
+    }
+    h->trt = kp.trt;
+    h->vec = default_vec(dim, precision);
+    h->bx = 128;
+    h->by = 1;
+    kp.xmax_load = kp.L.P - h->vec;
     kp.gbeta = h->gbeta; kp.omega = h->omega; kp.Th = h->prm.Th; kp.Tc = h->prm.Tc; kp.a_T = h->a_T;
     for (int a = 0; a < 3; ++a) {
         kp.body[a] = prm.body_force[a];
@@ -552,17 +585,14 @@ extern "C" int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp) {
 
 static cudaError_t launch_one_step(tlbm_t h) {
     const KParams& kp = h->kp;
-    const int vec = step_vec(h->dim, h->prec);
-    const int bx = 128;
+    const int vec = h->vec;
+    const int bx = h->bx, by = h->by;
     const int threads_x = (h->nx + vec - 1) / vec;
-    dim3 block(bx, 1, 1);
-    dim3 grid((threads_x + bx - 1) / bx, h->ny, h->dim == 3 ? h->nz : 1);
+    dim3 block(bx, by, 1);
+    dim3 grid((threads_x + bx - 1) / bx, (h->ny + by - 1) / by, h->dim == 3 ? h->nz : 1);
     const void* src = h->buf[h->cur];
     void* dst = h->buf[h->cur ^ 1];
-    cudaError_t e;
-    if (h->prec == TLBM_FP64) e = launch_step_fp64(h->dim, src, dst, kp, grid, block, h->stream);
-    else if (h->dim == 2) e = launch_step_2d(h->prec, src, dst, kp, grid, block, h->stream);
-    else e = launch_step_3d(h->prec, src, dst, kp, grid, block, h->stream);
+    cudaError_t e = launch_step(h->dim, h->prec, vec, h->trt != 0, src, dst, kp, grid, block, h->stream);
     if (e == cudaSuccess) {
         h->cur ^= 1;
         h->t += 1;
@@ -718,6 +748,34 @@ extern "C" int tlbm_set_populations(tlbm_t h, const double* host_f, const double
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     h->t = 0;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y) {
+    TLBM_CHECK_HANDLE(h);
+    const int v = vec > 0 ? vec : default_vec(h->dim, h->prec);
+    if (form < 0 || form > 2) return fail(h, TLBM_ERR_ARG, "form must be 0 (auto), 1 (MRT) or 2 (TRT)");
+    if (form == 2 && !h->kp.trt)
+        return fail(h, TLBM_ERR_ARG, "the relaxation rates are not of two-relaxation-time form");
+    const int trt = form == 1 ? 0 : h->kp.trt;
+    const int bx = block_x > 0 ? block_x : 128, by = block_y > 0 ? block_y : 1;
+    if (bx % 32 || bx * by > 1024) return fail(h, TLBM_ERR_ARG, "block_x must be a multiple of 32, bx*by <= 1024");
+    if (!step_variant_available(h->dim, h->prec, v, trt != 0))
+        return fail(h, TLBM_ERR_UNSUPPORTED, "step variant (vec %d, %s) not built", v, trt ? "TRT" : "MRT");
+    h->vec = v;
+    h->trt = trt;
+    h->bx = bx;
+    h->by = by;
+    h->kp.xmax_load = h->kp.L.P - v;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y) {
+    TLBM_CHECK_HANDLE(h);
+    if (vec) *vec = h->vec;
+    if (form) *form = h->trt ? 2 : 1;
+    if (block_x) *block_x = h->bx;
+    if (block_y) *block_y = h->by;
     return TLBM_OK;
 }
 

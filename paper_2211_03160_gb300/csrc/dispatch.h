@@ -1,5 +1,6 @@
-// Host-side launch entry points of the step kernels (one translation unit per
-// lattice dimension, FP64 in its own unit built without FMA contraction).
+// Host-side launch entry points of the step kernels.  Each translation unit
+// instantiates the variants of one (dimension, storage) family; the FP64 unit
+// is built without FMA contraction.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -7,15 +8,28 @@
 
 namespace tlbm {
 
-// prec: 0 FP64, 1 FP32, 2 FP16-offset, 3 BF16-offset (matches enum tlbm_prec)
-// Returns the vector width (nodes per thread) the step kernel uses.
-int step_vec(int dim, int prec);
+// prec: 0 FP64, 1 FP32, 2 FP16-offset, 3 BF16-offset (enum tlbm_prec).
+// vec: nodes per thread.  trt: two-relaxation-time form of the collision.
+// Returns cudaErrorInvalidValue if the variant is not compiled.
+cudaError_t launch_step(int dim, int prec, int vec, bool trt, const void* src, void* dst, const KParams& p,
+                        dim3 grid, dim3 block, cudaStream_t s);
+bool step_variant_available(int dim, int prec, int vec, bool trt);
 
-cudaError_t launch_step_2d(int prec, const void* src, void* dst, const KParams& p, dim3 grid, dim3 block,
-                           cudaStream_t s);
-cudaError_t launch_step_3d(int prec, const void* src, void* dst, const KParams& p, dim3 grid, dim3 block,
-                           cudaStream_t s);
-cudaError_t launch_step_fp64(int dim, const void* src, void* dst, const KParams& p, dim3 grid, dim3 block,
-                             cudaStream_t s);
+// per-unit entry points
+cudaError_t launch_step_2d_f32(int vec, bool trt, const void*, void*, const KParams&, dim3, dim3, cudaStream_t);
+cudaError_t launch_step_2d_f16(int prec, int vec, bool trt, const void*, void*, const KParams&, dim3, dim3,
+                               cudaStream_t);
+cudaError_t launch_step_3d_f32(int vec, bool trt, const void*, void*, const KParams&, dim3, dim3, cudaStream_t);
+cudaError_t launch_step_3d_f16(int prec, int vec, bool trt, const void*, void*, const KParams&, dim3, dim3,
+                               cudaStream_t);
+cudaError_t launch_step_f64(int dim, int vec, bool trt, const void*, void*, const KParams&, dim3, dim3,
+                            cudaStream_t);
 
 }  // namespace tlbm
+
+// Instantiate-and-launch helper: one case of a (vec, trt) switch.
+#define TLBM_STEP_CASE(DIM, S, VEC, TRT)                                                            \
+    if (vec == VEC && trt == TRT) {                                                                 \
+        tlbm::step_kernel<DIM, S, VEC, TRT><<<grid, block, 0, s>>>((const S*)src, (S*)dst, p);      \
+        return cudaGetLastError();                                                                  \
+    }

@@ -62,6 +62,12 @@ struct KParams {
     float Sf[MAXQ], Shf[MAXQ], Qf[7];
     float gbetaf, omegaf, Thf, Tcf, a_Tf, bodyf[3];
     float scale, inv_scale;  // offset-storage scale
+    // two-relaxation-time form of the same collision (valid when every even
+    // non-conserved rate equals sp and every odd one equals sm; the rates of the
+    // conserved moments do not enter the result)
+    int trt;
+    double sp, sm, shp, shm, qp, qm;
+    float spf, smf, shpf, shmf, qpf, qmf;
 };
 
 // ------------------------------------------------------------------ storage
@@ -105,6 +111,12 @@ __device__ __forceinline__ S from_c(C c) {
 // parameter accessors in the compute precision
 template <class C> struct PV;
 template <> struct PV<double> {
+    __device__ static double sp(const KParams& p) { return p.sp; }
+    __device__ static double sm(const KParams& p) { return p.sm; }
+    __device__ static double shp(const KParams& p) { return p.shp; }
+    __device__ static double shm(const KParams& p) { return p.shm; }
+    __device__ static double qp(const KParams& p) { return p.qp; }
+    __device__ static double qm(const KParams& p) { return p.qm; }
     __device__ static double S(const KParams& p, int k) { return p.S[k]; }
     __device__ static double Sh(const KParams& p, int k) { return p.Sh[k]; }
     __device__ static double Q(const KParams& p, int k) { return p.Q[k]; }
@@ -116,6 +128,12 @@ template <> struct PV<double> {
     __device__ static double body(const KParams& p, int a) { return p.body[a]; }
 };
 template <> struct PV<float> {
+    __device__ static float sp(const KParams& p) { return p.spf; }
+    __device__ static float sm(const KParams& p) { return p.smf; }
+    __device__ static float shp(const KParams& p) { return p.shpf; }
+    __device__ static float shm(const KParams& p) { return p.shmf; }
+    __device__ static float qp(const KParams& p) { return p.qpf; }
+    __device__ static float qm(const KParams& p) { return p.qmf; }
     __device__ static float S(const KParams& p, int k) { return p.Sf[k]; }
     __device__ static float Sh(const KParams& p, int k) { return p.Shf[k]; }
     __device__ static float Q(const KParams& p, int k) { return p.Qf[k]; }
@@ -271,9 +289,101 @@ template <int DIM> struct Lat;
 template <> struct Lat<2> { using F = D2Q9; using G = D2Q5; };
 template <> struct Lat<3> { using F = D3Q19; using G = D3Q7; };
 
+
+// Two-relaxation-time evaluation of the same collision.  When every even
+// non-conserved moment relaxes with sp and every odd one with sm, the MRT
+// operator M^-1 S M of Eq. (5) equals sp on the symmetric part and sm on the
+// antisymmetric part of each pair (i, ibar), and M^-1 (I - S/2) M Ftilde
+// splits the same way (the conserved moments' rates cancel out, see the MRT
+// form above).  Likewise for the thermal operator of Eq. (7).  Deviation form:
+//   E_i = f_eq,i - w_i = w_i [drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2)],
+//   G_i = w_i [3 (e - u).F + 9 (e.u)(e.F)]  (Guo).
 template <int DIM, class C>
+__device__ __forceinline__ void collide_trt(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q], const KParams& p) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    using P = PV<C>;
+    C drho = C(0), jx = C(0), jy = C(0), jz = C(0), T = C(0);
+    static_for<LF::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        drho += d[i];
+        if constexpr (LF::e(i, 0) == 1) jx += d[i];
+        if constexpr (LF::e(i, 0) == -1) jx -= d[i];
+        if constexpr (LF::e(i, 1) == 1) jy += d[i];
+        if constexpr (LF::e(i, 1) == -1) jy -= d[i];
+        if constexpr (LF::e(i, 2) == 1) jz += d[i];
+        if constexpr (LF::e(i, 2) == -1) jz -= d[i];
+    });
+    static_for<LG::Q>([&](auto ii) { T += g[decltype(ii)::value]; });
+    const C rho = C(1) + drho;
+    const C buoy = P::gbeta(p) * T;
+    const C Fx = rho * P::body(p, 0);
+    const C Fy = rho * (DIM == 2 ? buoy + P::body(p, 1) : P::body(p, 1));
+    const C Fz = DIM == 3 ? rho * (buoy + P::body(p, 2)) : C(0);
+    const C ir = C(1) / rho;
+    const C ux = (jx + C(0.5) * Fx) * ir;
+    const C uy = (jy + C(0.5) * Fy) * ir;
+    const C uz = DIM == 3 ? (jz + C(0.5) * Fz) * ir : C(0);
+    const C sp = P::sp(p), sm = P::sm(p), shp = P::shp(p), shm = P::shm(p);
+    const C uu15 = C(1.5) * (ux * ux + uy * uy + uz * uz);
+    const C uF3 = C(3) * (ux * Fx + uy * Fy + uz * Fz);
+    // rest population
+    {
+        constexpr C w0 = weight<LF, C>(0);
+        const C E0 = w0 * (drho - rho * uu15);
+        const C G0 = -w0 * uF3;
+        d[0] = d[0] - sp * (d[0] - E0) + shp * G0;
+    }
+    static_for<LF::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        constexpr int o = LF::opp(i);
+        if constexpr (i != 0 && i < o) {
+            constexpr int ex = LF::e(i, 0), ey = LF::e(i, 1), ez = LF::e(i, 2);
+            constexpr C w = weight<LF, C>(i);
+            C eu = C(0), eF = C(0);
+            if constexpr (ex != 0) { eu += C(ex) * ux; eF += C(ex) * Fx; }
+            if constexpr (ey != 0) { eu += C(ey) * uy; eF += C(ey) * Fy; }
+            if constexpr (ez != 0) { eu += C(ez) * uz; eF += C(ez) * Fz; }
+            const C Es = w * (drho + rho * (C(4.5) * eu * eu - uu15));
+            const C Ea = w * C(3) * rho * eu;
+            const C Gs = w * (C(9) * eu * eF - uF3);
+            const C Ga = w * C(3) * eF;
+            const C ds = C(0.5) * (d[i] + d[o]);
+            const C da = C(0.5) * (d[i] - d[o]);
+            const C A = shp * Gs - sp * (ds - Es);
+            const C B = shm * Ga - sm * (da - Ea);
+            d[i] = d[i] + A + B;
+            d[o] = d[o] + A - B;
+        }
+    });
+    // thermal: g_eq,i = wT T + (e.u) T / 2 on the moving links, wT = omega/2
+    const C qp = P::qp(p), qm = P::qm(p);
+    const C wT = C(0.5) * P::omega(p);
+    const C geqs = wT * T;
+    {
+        const C g0eq = T - C(LG::Q - 1) * geqs;
+        g[0] = g[0] - qp * (g[0] - g0eq);
+    }
+    static_for<LG::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        constexpr int o = LG::opp(i);
+        if constexpr (i != 0 && i < o) {
+            constexpr int ex = LG::e(i, 0), ey = LG::e(i, 1), ez = LG::e(i, 2);
+            const C eu = ex != 0 ? C(ex) * ux : (ey != 0 ? C(ey) * uy : C(ez) * uz);
+            const C gs = C(0.5) * (g[i] + g[o]);
+            const C ga = C(0.5) * (g[i] - g[o]);
+            const C A = -qp * (gs - geqs);
+            const C B = -qm * (ga - C(0.5) * eu * T);
+            g[i] = g[i] + A + B;
+            g[o] = g[o] + A - B;
+        }
+    });
+}
+
+template <int DIM, bool TRT, class C>
 __device__ __forceinline__ void collide(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q], const KParams& p) {
-    if constexpr (DIM == 2) collide_2d<C>(d, g, p);
+    if constexpr (TRT) collide_trt<DIM, C>(d, g, p);
+    else if constexpr (DIM == 2) collide_2d<C>(d, g, p);
     else collide_3d<C>(d, g, p);
 }
 
@@ -468,7 +578,7 @@ __device__ __forceinline__ void pull_node_vec(const S* __restrict__ src, const K
 
 // One thread updates VEC consecutive nodes of one row.  blockDim.x must be a
 // multiple of 32 so that a warp covers 32*VEC consecutive nodes of one row.
-template <int DIM, class S, int VEC>
+template <int DIM, class S, int VEC, bool TRT>
 __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
@@ -480,6 +590,7 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
     const int z = DIM == 3 ? (int)blockIdx.z : 0;
     if (y >= L.ny) return;  // uniform across the warp
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
+    if (x0 - lane * VEC >= L.nx) return;  // the whole warp lies past the row end
     const int x0ld = min(x0, p.xmax_load);
     const C scale = ScaleOf<C>::s(p);
 
@@ -493,7 +604,7 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
         for (int i = 0; i < QF; ++i) fd[i] = f[i][k];
 #pragma unroll
         for (int i = 0; i < QG; ++i) gd[i] = g[i][k];
-        collide<DIM, C>(fd, gd, p);
+        collide<DIM, TRT, C>(fd, gd, p);
 #pragma unroll
         for (int i = 0; i < QF; ++i) f[i][k] = fd[i];
 #pragma unroll

@@ -1,0 +1,13 @@
+// D3Q19 + D3Q7 fused step, FP32 storage.
+#include "dispatch.h"
+
+namespace tlbm {
+cudaError_t launch_step_3d_f32(int vec, bool trt, const void* src, void* dst, const KParams& p, dim3 grid,
+                               dim3 block, cudaStream_t s) {
+    TLBM_STEP_CASE(3, float, 4, true)
+    TLBM_STEP_CASE(3, float, 2, true)
+    TLBM_STEP_CASE(3, float, 1, true)
+    TLBM_STEP_CASE(3, float, 2, false)
+    return cudaErrorInvalidValue;
+}
+}  // namespace tlbm

@@ -76,6 +76,9 @@ _SIGS = {
                                               C.c_void_p, C.c_void_p]),
     "tlbm_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "tlbm_derived": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
+    "tlbm_set_variant": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "tlbm_get_variant": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]),
     "tlbm_last_error": (C.c_char_p, [C.c_void_p]),
     "tlbm_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "tlbm_destroy": (None, [C.c_void_p]),
@@ -208,6 +211,16 @@ def tlbm_derived(h) -> list:
     return list(buf[: n.value])
 
 
+def tlbm_set_variant(h, vec=0, form=0, block_x=0, block_y=0):
+    _check(h, lib().tlbm_set_variant(h, int(vec), int(form), int(block_x), int(block_y)))
+
+
+def tlbm_get_variant(h):
+    v = [C.c_int() for _ in range(4)]
+    _check(h, lib().tlbm_get_variant(h, *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
 def tlbm_last_error(h) -> str:
     m = lib().tlbm_last_error(h)
     return m.decode() if m else ""
@@ -326,6 +339,13 @@ class Sim:
         g = np.ascontiguousarray(g, dtype=np.float64)
         assert f.size == self.qf * self.N and g.size == self.qg * self.N
         tlbm_set_populations(self.h, f, g)
+
+    def set_variant(self, vec=0, form=0, block_x=0, block_y=0):
+        tlbm_set_variant(self.h, vec, form, block_x, block_y)
+
+    @property
+    def variant(self):
+        return tlbm_get_variant(self.h)
 
     @property
     def launches(self):

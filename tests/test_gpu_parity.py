@@ -90,30 +90,66 @@ EDGE_CASES = [
 ]
 
 
+# every compiled step variant: (vec, form) with form 1 = general MRT, 2 = TRT evaluation
+VARIANTS = {
+    (D2, FP32): [(4, 2), (2, 2), (1, 2), (4, 1)], (D2, FP16): [(8, 2), (4, 2), (2, 2), (8, 1)],
+    (D2, BF16): [(8, 2), (4, 2), (2, 2), (8, 1)], (D2, FP64): [(2, 2), (1, 2), (2, 1)],
+    (D3, FP32): [(4, 2), (2, 2), (1, 2), (2, 1)], (D3, FP16): [(4, 2), (2, 2), (1, 2), (4, 1)],
+    (D3, BF16): [(4, 2), (2, 2), (1, 2), (4, 1)], (D3, FP64): [(1, 2), (2, 2), (1, 1)],
+}
+
+
 @pytest.mark.parametrize("prec", [FP64, FP32, FP16, BF16])
 @pytest.mark.parametrize("lattice,shape,walls,pm", EDGE_CASES)
 def test_one_step_random_populations(T, O, prec, lattice, shape, walls, pm):
-    """Random populations set through the ABI; one and three steps must match
-    the oracle started from the same values as the GPU stores them."""
+    """Random populations set through the ABI; one and then two more steps must
+    match the oracle started from the same values as the GPU stores them, for
+    every compiled kernel variant (nodes per thread, MRT or TRT evaluation)."""
     nx, ny, nz = shape
     kw = dict(walls=walls, periodic_mask=pm)
-    g = T.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec, **kw)
     o = O.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1, **kw)
     qf, qg = (9, 5) if lattice == D2 else (19, 7)
     seed = 7 + 13 * lattice + 3 * walls + pm + 100 * prec + nx
     f = inputs.uniform_array(seed, (qf,) + o.shape, 0.02, 0.2)
     gg = inputs.uniform_array(seed + 1, (qg,) + o.shape, -0.1, 0.1)
-    g.set_populations(f, gg)
-    f0, g0 = g.get_populations()  # as stored in the GPU precision
-    o.set_populations(f0, g0)
-    for n in (1, 2):
-        g.step(n)
-        o.step(n)
-        fg, ggg = g.get_populations()
-        fo, go = o.get_populations()
-        ef = np.abs(fg - fo).max() / np.abs(fo).max()
-        eg = np.abs(ggg - go).max() / np.abs(go).max()
-        assert ef < TOL1[prec] * n and eg < TOL1[prec] * n, (n, ef, eg)
+    ref = None
+    for vec, form in VARIANTS[(lattice, prec)]:
+        g = T.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec, **kw)
+        g.set_variant(vec, form)
+        assert g.variant[:2] == (vec, form)
+        g.set_populations(f, gg)
+        f0, g0 = g.get_populations()  # as stored in the GPU precision
+        if ref is None:
+            o.set_populations(f0, g0)
+            ref = []
+            for n in (1, 2):
+                o.step(n)
+                ref.append(o.get_populations())
+        for (fo, go), n in zip(ref, (1, 2)):
+            g.step(n)
+            fg, ggg = g.get_populations()
+            ef = np.abs(fg - fo).max() / np.abs(fo).max()
+            eg = np.abs(ggg - go).max() / np.abs(go).max()
+            assert ef < TOL1[prec] * n and eg < TOL1[prec] * n, (vec, form, n, ef, eg)
+        g.close()
+
+
+def test_variants_agree_bitwise(T):
+    """Nodes per thread and block shape change only how loads are issued: the
+    TRT variants give bit-identical states, and so do the MRT variants."""
+    for lattice, shape, prec in ((D2, (301, 45, 1), FP32), (D2, (301, 45, 1), FP16), (D3, (77, 21, 13), FP32),
+                                 (D3, (77, 21, 13), BF16)):
+        outs = []
+        for vec, form in [v for v in VARIANTS[(lattice, prec)] if v[1] == 2]:
+            for bx, by in ((128, 1), (64, 2), (32, 4)):
+                g = T.Sim(*shape, lattice=lattice, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
+                g.set_variant(vec, 2, bx, by)
+                g.init(11, 1e-3)
+                g.step(20)
+                outs.append(g.get_populations())
+                g.close()
+        for f, gg in outs[1:]:
+            assert np.array_equal(f, outs[0][0]) and np.array_equal(gg, outs[0][1])
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32, FP16, BF16])
@@ -126,15 +162,16 @@ def test_init_matches_oracle(T, O, prec, lattice, shape):
     g.init(42, 1e-3)
     o.init(42, 1e-3)
     tg, to = _fields(g)["T"], o.macros()["T"]
-    tol = {FP64: 1e-16, FP32: 1e-7, FP16: 1e-3, BF16: 8e-3}[prec]
+    tol = {FP64: 2.5e-16, FP32: 1e-7, FP16: 1e-3, BF16: 8e-3}[prec]
     assert np.abs(tg - to).max() < tol
 
 
 # ------------------------------------------------------------------ reduced precision vs FP64
 
-@pytest.mark.parametrize("prec,tol_T,tol_u", [(FP32, 2e-5, 2e-3), (FP16, 3e-2, 0.25), (BF16, 0.1, 1.0)])
+@pytest.mark.parametrize("prec,tol_T,tol_u", [(FP32, 2e-5, 1e-3), (FP16, 3e-2, 0.25), (BF16, 0.1, 1.0)])
 def test_reduced_precision_fields_vs_oracle(T, O, prec, tol_T, tol_u):
-    """129^2, Ra = 1e5, 400 steps: field error max|a - b| / max|b| per field."""
+    """129^2, Ra = 1e5, 400 steps: field error max|a - b| / max|b| (velocity
+    components scaled by the largest velocity component)."""
     g = T.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec)
     o = O.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1)
     g.init(1, 1e-3)
@@ -142,7 +179,10 @@ def test_reduced_precision_fields_vs_oracle(T, O, prec, tol_T, tol_u):
     g.step(400)
     o.step(400)
     a, b = _fields(g), o.macros()
-    rel = {k: float(np.abs(a[k] - b[k]).max() / np.abs(b[k]).max()) for k in ("T", "ux", "uy")}
+    umax = max(np.abs(b["ux"]).max(), np.abs(b["uy"]).max())
+    rel = {"T": float(np.abs(a["T"] - b["T"]).max() / np.abs(b["T"]).max()),
+           "ux": float(np.abs(a["ux"] - b["ux"]).max() / umax),
+           "uy": float(np.abs(a["uy"] - b["uy"]).max() / umax)}
     print("field rel err", prec, rel)
     assert rel["T"] < tol_T and rel["ux"] < tol_u and rel["uy"] < tol_u, rel
 
@@ -204,7 +244,7 @@ def test_divergence_is_reported(T):
     f = np.zeros((9, 16, 16))
     gg = np.zeros((5, 16, 16))
     f[0] = 0.5
-    f[1] = 0.5  # u_x = 0.5/1.0 at every node
+    f[1] = 0.6  # u_x = 0.6/1.1 > 0.5 at every node
     g.set_populations(f, gg)
     div, _ = g.status()
     assert div
