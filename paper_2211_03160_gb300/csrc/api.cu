@@ -762,6 +762,12 @@ extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bl
     if (bx % 32 || bx * by > 1024) return fail(h, TLBM_ERR_ARG, "block_x must be a multiple of 32, bx*by <= 1024");
     if (!step_variant_available(h->dim, h->prec, v, trt != 0))
         return fail(h, TLBM_ERR_UNSUPPORTED, "step variant (vec %d, %s) not built", v, trt ? "TRT" : "MRT");
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, step_function(h->dim, h->prec, v, trt != 0));
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncGetAttributes");
+    if (bx * by > fa.maxThreadsPerBlock)
+        return fail(h, TLBM_ERR_ARG, "block of %d threads exceeds the variant's limit of %d", bx * by,
+                    fa.maxThreadsPerBlock);
     h->vec = v;
     h->trt = trt;
     h->bx = bx;

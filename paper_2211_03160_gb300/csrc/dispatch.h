@@ -14,6 +14,8 @@ namespace tlbm {
 cudaError_t launch_step(int dim, int prec, int vec, bool trt, const void* src, void* dst, const KParams& p,
                         dim3 grid, dim3 block, cudaStream_t s);
 bool step_variant_available(int dim, int prec, int vec, bool trt);
+// device function of a compiled variant (for cudaFuncGetAttributes), or nullptr
+const void* step_function(int dim, int prec, int vec, bool trt);
 
 // per-unit entry points
 cudaError_t launch_step_2d_f32(int vec, bool trt, const void*, void*, const KParams&, dim3, dim3, cudaStream_t);
@@ -24,6 +26,11 @@ cudaError_t launch_step_3d_f16(int prec, int vec, bool trt, const void*, void*, 
                                cudaStream_t);
 cudaError_t launch_step_f64(int dim, int vec, bool trt, const void*, void*, const KParams&, dim3, dim3,
                             cudaStream_t);
+const void* func_step_2d_f32(int vec, bool trt);
+const void* func_step_2d_f16(int prec, int vec, bool trt);
+const void* func_step_3d_f32(int vec, bool trt);
+const void* func_step_3d_f16(int prec, int vec, bool trt);
+const void* func_step_f64(int dim, int vec, bool trt);
 
 }  // namespace tlbm
 
@@ -33,3 +40,6 @@ cudaError_t launch_step_f64(int dim, int vec, bool trt, const void*, void*, cons
         tlbm::step_kernel<DIM, S, VEC, TRT><<<grid, block, 0, s>>>((const S*)src, (S*)dst, p);      \
         return cudaGetLastError();                                                                  \
     }
+
+#define TLBM_STEP_FUNC(DIM, S, VEC, TRT) \
+    if (vec == VEC && trt == TRT) return (const void*)&tlbm::step_kernel<DIM, S, VEC, TRT>;

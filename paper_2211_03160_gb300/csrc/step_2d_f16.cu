@@ -3,7 +3,7 @@
 
 namespace tlbm {
 cudaError_t launch_step_2d_f16(int prec, int vec, bool trt, const void* src, void* dst, const KParams& p,
-                               dim3 grid, dim3 block, cudaStream_t s) {
+                        dim3 grid, dim3 block, cudaStream_t s) {
     if (prec == 2) {
         TLBM_STEP_CASE(2, __half, 8, true)
         TLBM_STEP_CASE(2, __half, 4, true)
@@ -16,5 +16,20 @@ cudaError_t launch_step_2d_f16(int prec, int vec, bool trt, const void* src, voi
         TLBM_STEP_CASE(2, __nv_bfloat16, 8, false)
     }
     return cudaErrorInvalidValue;
+}
+
+const void* func_step_2d_f16(int prec, int vec, bool trt) {
+    if (prec == 2) {
+        TLBM_STEP_FUNC(2, __half, 8, true)
+        TLBM_STEP_FUNC(2, __half, 4, true)
+        TLBM_STEP_FUNC(2, __half, 2, true)
+        TLBM_STEP_FUNC(2, __half, 8, false)
+    } else {
+        TLBM_STEP_FUNC(2, __nv_bfloat16, 8, true)
+        TLBM_STEP_FUNC(2, __nv_bfloat16, 4, true)
+        TLBM_STEP_FUNC(2, __nv_bfloat16, 2, true)
+        TLBM_STEP_FUNC(2, __nv_bfloat16, 8, false)
+    }
+    return nullptr;
 }
 }  // namespace tlbm

@@ -3,11 +3,19 @@
 
 namespace tlbm {
 cudaError_t launch_step_2d_f32(int vec, bool trt, const void* src, void* dst, const KParams& p, dim3 grid,
-                               dim3 block, cudaStream_t s) {
+                        dim3 block, cudaStream_t s) {
     TLBM_STEP_CASE(2, float, 4, true)
     TLBM_STEP_CASE(2, float, 2, true)
     TLBM_STEP_CASE(2, float, 1, true)
     TLBM_STEP_CASE(2, float, 4, false)
     return cudaErrorInvalidValue;
+}
+
+const void* func_step_2d_f32(int vec, bool trt) {
+    TLBM_STEP_FUNC(2, float, 4, true)
+    TLBM_STEP_FUNC(2, float, 2, true)
+    TLBM_STEP_FUNC(2, float, 1, true)
+    TLBM_STEP_FUNC(2, float, 4, false)
+    return nullptr;
 }
 }  // namespace tlbm

@@ -18,6 +18,25 @@ cudaError_t launch_step_f64(int dim, int vec, bool trt, const void* src, void* d
     return cudaErrorInvalidValue;
 }
 
+const void* func_step_f64(int dim, int vec, bool trt) {
+    if (dim == 2) {
+        TLBM_STEP_FUNC(2, double, 2, true)
+        TLBM_STEP_FUNC(2, double, 1, true)
+        TLBM_STEP_FUNC(2, double, 2, false)
+    } else {
+        TLBM_STEP_FUNC(3, double, 1, true)
+        TLBM_STEP_FUNC(3, double, 2, true)
+        TLBM_STEP_FUNC(3, double, 1, false)
+    }
+    return nullptr;
+}
+
+const void* step_function(int dim, int prec, int vec, bool trt) {
+    if (prec == 0) return func_step_f64(dim, vec, trt);
+    if (dim == 2) return prec == 1 ? func_step_2d_f32(vec, trt) : func_step_2d_f16(prec, vec, trt);
+    return prec == 1 ? func_step_3d_f32(vec, trt) : func_step_3d_f16(prec, vec, trt);
+}
+
 bool step_variant_available(int dim, int prec, int vec, bool trt) {
     static const int table[][4] = {
         // dim, prec, vec, trt
