@@ -181,6 +181,11 @@ def workload(name: str):
         "2d_8193_fp64": (2, 8193, 8193, 1, 1e8, "fp64", 2),
         "3d_385_fp32": (3, 385, 385, 385, 1e7, "fp32", 3),
         "3d_385_fp16": (3, 385, 385, 385, 1e7, "fp16", 3),
+        # smaller cases of the same physics for profiler captures (still > L2)
+        "2d_4097_fp32": (2, 4097, 4097, 1, 1e8, "fp32", 2),
+        "2d_4097_fp16": (2, 4097, 4097, 1, 1e8, "fp16", 2),
+        "3d_257_fp32": (3, 257, 257, 257, 1e7, "fp32", 3),
+        "3d_257_fp16": (3, 257, 257, 257, 1e7, "fp16", 3),
     }
     return table[name]
 

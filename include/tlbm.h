@@ -179,7 +179,7 @@ TLBM_API int tlbm_derived(tlbm_t h, double* out, int cap, int* count);
  * form = 0 automatic (two-relaxation-time evaluation when the rates allow it,
  * else the general MRT), 1 general MRT, 2 two-relaxation-time (TLBM_ERR_ARG if
  * the rates are not of that form); block_x (multiple of 32) x block_y threads
- * per block (0 = default 128 x 1).  All variants compute the same collision;
+ * per block (0 = the tuned default of the lattice and precision).  All variants compute the same collision;
  * TLBM_ERR_UNSUPPORTED if the variant is not compiled. */
 TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y);
 /* Current variant (form reported as 1 MRT or 2 TRT).  Outputs may be NULL. */

@@ -12,6 +12,7 @@
 
 #include "../../include/tlbm.h"
 #include "dispatch.h"
+#include "handle.h"
 
 using namespace tlbm;
 
@@ -28,27 +29,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
-struct tlbm_s {
-    int nx, ny, nz, dim, lattice, prec;
-    int qf, qg;
-    double Ra, Pr, Ma;
-    tlbm_params prm;
-    double U, H, nu, alpha, gbeta, a_T, omega;
-    double S[MAXQ], Q[7];
-    KParams kp;
-    int vec, trt, bx, by;      // step kernel variant and block shape
-    size_t elem;               // bytes per stored value
-    size_t popset_bytes;       // one population buffer (f planes then g planes)
-    size_t red_off, res_off, stage_off, total_bytes;
-    char* mem;                 // bound device block
-    size_t mem_bytes;
-    void* buf[2];
-    int cur;                   // buffer holding the current state
-    int64_t t;
-    cudaStream_t stream;
-    int64_t launches;
-    char err[256];
-};
+
 
 // ------------------------------------------------------------------ errors
 
@@ -376,11 +357,26 @@ extern "C" void tlbm_default_params(tlbm_params* p) {
 
 static double pick(double v, double d) { return std::isnan(v) ? d : v; }
 
-// nodes per thread of the step kernel unless tuned otherwise
-static int default_vec(int dim, int prec) {
-    if (dim == 2) return prec == TLBM_FP64 ? 2 : (prec == TLBM_FP32 ? 4 : 8);
-    return prec == TLBM_FP64 ? 1 : (prec == TLBM_FP32 ? 2 : 4);
+// Default step variant per (dimension, storage): nodes per thread and block
+// shape, from a sweep on GB300 at 8193^2 (2D) and 385^3 (3D).
+struct VariantDefault {
+    int vec, bx, by;
+};
+static VariantDefault default_variant(int dim, int prec) {
+    if (dim == 2) {
+        switch (prec) {
+        case TLBM_FP64: return {2, 64, 1};
+        case TLBM_FP32: return {4, 32, 1};
+        default: return {4, 32, 2};
+        }
+    }
+    switch (prec) {
+    case TLBM_FP64: return {1, 32, 4};
+    case TLBM_FP32: return {2, 32, 4};
+    default: return {1, 32, 4};
+    }
 }
+static int default_vec(int dim, int prec) { return default_variant(dim, prec).vec; }
 
 extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, double Ra, double Pr, double Ma,
                            int precision, const tlbm_params* pin) {
@@ -490,9 +486,9 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
         kp.qpf = (float)kp.qp; kp.qmf = (float)kp.qm;
     }
     h->trt = kp.trt;
-    h->vec = default_vec(dim, precision);
-    h->bx = 128;
-    h->by = 1;
+    h->vec = default_variant(dim, precision).vec;
+    h->bx = default_variant(dim, precision).bx;
+    h->by = default_variant(dim, precision).by;
     kp.xmax_load = kp.L.P - h->vec;
     kp.gbeta = h->gbeta; kp.omega = h->omega; kp.Th = h->prm.Th; kp.Tc = h->prm.Tc; kp.a_T = h->a_T;
     for (int a = 0; a < 3; ++a) {
@@ -758,7 +754,8 @@ extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bl
     if (form == 2 && !h->kp.trt)
         return fail(h, TLBM_ERR_ARG, "the relaxation rates are not of two-relaxation-time form");
     const int trt = form == 1 ? 0 : h->kp.trt;
-    const int bx = block_x > 0 ? block_x : 128, by = block_y > 0 ? block_y : 1;
+    const int bx = block_x > 0 ? block_x : default_variant(h->dim, h->prec).bx;
+    const int by = block_y > 0 ? block_y : default_variant(h->dim, h->prec).by;
     if (bx % 32 || bx * by > 1024) return fail(h, TLBM_ERR_ARG, "block_x must be a multiple of 32, bx*by <= 1024");
     if (!step_variant_available(h->dim, h->prec, v, trt != 0))
         return fail(h, TLBM_ERR_UNSUPPORTED, "step variant (vec %d, %s) not built", v, trt ? "TRT" : "MRT");

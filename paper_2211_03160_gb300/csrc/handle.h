@@ -1,0 +1,29 @@
+// Host-side state of a tlbm handle (private to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tlbm.h"
+#include "kernels.cuh"
+
+struct tlbm_s {
+    int nx, ny, nz, dim, lattice, prec;
+    int qf, qg;
+    double Ra, Pr, Ma;
+    tlbm_params prm;
+    double U, H, nu, alpha, gbeta, a_T, omega;
+    double S[tlbm::MAXQ], Q[7];
+    tlbm::KParams kp;
+    int vec, trt, bx, by;      // step kernel variant and block shape
+    size_t elem;               // bytes per stored value
+    size_t popset_bytes;       // one population buffer (f planes then g planes)
+    size_t red_off, res_off, stage_off, total_bytes;
+    char* mem;                 // bound device block
+    size_t mem_bytes;
+    void* buf[2];
+    int cur;                   // buffer holding the current state
+    int64_t t;
+    cudaStream_t stream;
+    int64_t launches;
+    char err[256];
+};
