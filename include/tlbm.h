@@ -124,7 +124,15 @@ TLBM_API int tlbm_required_bytes(tlbm_t h, size_t* bytes);
 
 /* Bind a caller-owned device block of at least tlbm_required_bytes() bytes,
  * 256-byte aligned.  The library never frees it; it must outlive the handle's
- * use.  Re-binding moves nothing: call tlbm_init or tlbm_set_populations after. */
+ * use.  Re-binding moves nothing: call tlbm_init or tlbm_set_populations after.
+ * The block starts with two population buffers of B bytes each, then scratch:
+ *   P = 32 * ceil((nx + 16) / 32),  R = (ny + 2) * (nz + 2) in 3D, ny + 2 in 2D,
+ *   plane = 64 * ceil((128 + R * P) / 64) elements,
+ *   B = 256 * ceil((qf + qg) * plane * element_bytes / 256),
+ * with (qf, qg) = (9, 5) or (19, 7) and element_bytes 8, 4, 2, 2 for FP64, FP32,
+ * FP16, BF16.  The current state is buffer 0 after tlbm_init or
+ * tlbm_set_populations and after every even number of steps since; buffer 1
+ * after an odd number. */
 TLBM_API int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes);
 
 /* Stream for all later work (a cudaStream_t; NULL = legacy default stream). */
@@ -184,6 +192,29 @@ TLBM_API int tlbm_derived(tlbm_t h, double* out, int cap, int* count);
 TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y);
 /* Current variant (form reported as 1 MRT or 2 TRT).  Outputs may be NULL. */
 TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y);
+
+/* FP64 diagnostic sums of a population state without any device memory from
+ * the caller beyond the state itself (the paper has no counterpart; this is a
+ * library service).  For callers that hold a state but cannot allocate device
+ * memory, e.g. a process that maps another process's state through CUDA IPC on
+ * a GPU where it may not allocate, or code running while another thread holds
+ * a global-mode stream capture (cudaMalloc is refused until it ends).
+ *   h:     handle describing the cell, precision and parameters; it needs bound
+ *          memory only when state is NULL.
+ *   state: device pointer to a population buffer laid out as described at
+ *          tlbm_bind_memory for a handle created with the same arguments, or
+ *          NULL for h's current state.
+ *   out:   host array of 6 doubles: sum u_h T, sum 1/2 rho |u|^2, sum rho,
+ *          max |u|^2, non-finite flag (1.0 if any), sum T; u_h as in tlbm_nusselt.
+ * The block partial sums live in a static device array compiled into the
+ * library (8192 slots, 384 KiB per device that loads the library, kept until
+ * the process exits), so the call allocates nothing; cells of more than
+ * 8192 * 16384 = 134,217,728 nodes are rejected with TLBM_ERR_ARG.  The first
+ * call on a device looks up that array's device address, so make it before any
+ * stream capture.  Every call shares the array: calls that overlap on the GPU
+ * (other streams, handles or threads) race.  Runs on h's stream and
+ * synchronises it. */
+TLBM_API int tlbm_reduce_noalloc(tlbm_t h, const void* state, double* out);
 
 /* Text of the last error on this handle ("" if none); valid until the next call
  * on the handle.  A NULL handle returns the last error of a failed tlbm_create

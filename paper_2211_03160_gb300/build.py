@@ -27,6 +27,7 @@ UNITS = {
     "step_3d_f32.cu": [],
     "step_3d_f16.cu": [],
     "step_fp64.cu": ["--fmad=false"],
+    "noalloc.cu": [],
 }
 
 

@@ -79,6 +79,7 @@ _SIGS = {
     "tlbm_set_variant": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "tlbm_get_variant": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int)]),
+    "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_last_error": (C.c_char_p, [C.c_void_p]),
     "tlbm_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "tlbm_destroy": (None, [C.c_void_p]),
@@ -219,6 +220,14 @@ def tlbm_get_variant(h):
     v = [C.c_int() for _ in range(4)]
     _check(h, lib().tlbm_get_variant(h, *[C.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def tlbm_reduce_noalloc(h, state_ptr=None) -> list:
+    """The six FP64 diagnostic sums of a state with no device allocation (see
+    include/tlbm.h); state_ptr is a device address or None for the current state."""
+    out = (C.c_double * 6)()
+    _check(h, lib().tlbm_reduce_noalloc(h, None if state_ptr is None else C.c_void_p(state_ptr), out))
+    return list(out)
 
 
 def tlbm_last_error(h) -> str:
