@@ -486,6 +486,25 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
         kp.qpf = (float)kp.qp; kp.qmf = (float)kp.qm;
     }
     h->trt = kp.trt;
+    {
+        // per-population pull / store offsets (elements, relative to a node's own
+        // slot in plane 0): plane j, shifted back by the population's e_y, e_z
+        // (the x-shift is taken by the kernel's loads)
+        const long long P = kp.L.P, RP = (long long)(ny + 2) * kp.L.P;
+        const int qf = h->qf;
+        for (int j = 0; j < h->qf + h->qg; ++j) {
+            int ey, ez;
+            if (dim == 2) {
+                ey = j < qf ? D2Q9::e(j, 1) : D2Q5::e(j - qf, 1);
+                ez = 0;
+            } else {
+                ey = j < qf ? D3Q19::e(j, 1) : D3Q7::e(j - qf, 1);
+                ez = j < qf ? D3Q19::e(j, 2) : D3Q7::e(j - qf, 2);
+            }
+            kp.soff[j] = (long long)j * kp.L.plane;
+            kp.loff[j] = kp.soff[j] - ey * P - ez * RP;
+        }
+    }
     h->vec = default_variant(dim, precision).vec;
     h->bx = default_variant(dim, precision).bx;
     h->by = default_variant(dim, precision).by;

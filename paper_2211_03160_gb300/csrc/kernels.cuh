@@ -68,6 +68,11 @@ struct KParams {
     int trt;
     double sp, sm, shp, shm, qp, qm;
     float spf, smf, shpf, shmf, qpf, qmf;
+    // element offsets, relative to a node's own slot in plane 0, of the slot
+    // each population j (flow planes first, then thermal) is pulled from, and
+    // of the plane it is stored to
+    long long loff[2 * MAXQ];
+    long long soff[2 * MAXQ];
 };
 
 // ------------------------------------------------------------------ storage
@@ -184,6 +189,10 @@ template <> struct ScaleOf<double> {
 };
 
 // ------------------------------------------------------------------ collision
+
+// 1/x, correctly rounded in both precisions
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Macroscopic moments of one node from deviations (§2.2):
 // rho = 1 + sum d, T = sum g, F = rho (g beta T ghat + a), u = (sum e f + F/2)/rho.
@@ -320,7 +329,7 @@ __device__ __forceinline__ void collide_trt(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<D
     const C Fx = rho * P::body(p, 0);
     const C Fy = rho * (DIM == 2 ? buoy + P::body(p, 1) : P::body(p, 1));
     const C Fz = DIM == 3 ? rho * (buoy + P::body(p, 2)) : C(0);
-    const C ir = C(1) / rho;
+    const C ir = recip(rho);
     const C ux = (jx + C(0.5) * Fx) * ir;
     const C uy = (jy + C(0.5) * Fy) * ir;
     const C uz = DIM == 3 ? (jz + C(0.5) * Fz) * ir : C(0);
@@ -460,29 +469,29 @@ __device__ __forceinline__ void st_vec(S* __restrict__ p, const S (&v)[VEC]) {
 }
 
 // Load the VEC consecutive stored values that nodes x0 .. x0+VEC-1 pull in a
-// direction with x-component EX, from the source row `row` (slot index of x = 0
-// of the row y - e_y, z - e_z).  The aligned vector at x0 is loaded and shifted
-// by one element through a warp shuffle; the warp's edge lane fetches the one
-// element beyond its vector directly.  All 32 lanes must call this together.
+// direction with x-component EX; `q` points at the slot of the source row
+// (y - e_y, z - e_z) under x0 (16-byte aligned for VEC > 1).  The aligned
+// vector at q is loaded and shifted by one element through a warp shuffle; the
+// warp's edge lane fetches the one element beyond its vector directly.  All 32
+// lanes must call this together.
 template <class S, int VEC, int EX, class C>
-__device__ __forceinline__ void pull_row(const S* __restrict__ plane, long long row, int x0ld, int lane,
-                                         C (&out)[VEC]) {
+__device__ __forceinline__ void pull_row(const S* __restrict__ q, int lane, C (&out)[VEC]) {
     S v[VEC];
-    ld_vec<S, VEC>(plane + row + x0ld, v);
+    ld_vec<S, VEC>(q, v);
     if constexpr (EX == 0) {
 #pragma unroll
         for (int k = 0; k < VEC; ++k) out[k] = to_c<C>(v[k]);
     } else if constexpr (EX == 1) {
         // node x pulls from x - 1
         C left = __shfl_up_sync(0xffffffffu, to_c<C>(v[VEC - 1]), 1);
-        if (lane == 0) left = to_c<C>(plane[row + x0ld - 1]);
+        if (lane == 0) left = to_c<C>(q[-1]);
         out[0] = left;
 #pragma unroll
         for (int k = 1; k < VEC; ++k) out[k] = to_c<C>(v[k - 1]);
     } else {
         // node x pulls from x + 1
         C right = __shfl_down_sync(0xffffffffu, to_c<C>(v[0]), 1);
-        if (lane == 31) right = to_c<C>(plane[row + x0ld + VEC]);
+        if (lane == 31) right = to_c<C>(q[VEC]);
 #pragma unroll
         for (int k = 0; k < VEC - 1; ++k) out[k] = to_c<C>(v[k + 1]);
         out[VEC - 1] = right;
@@ -547,33 +556,53 @@ __device__ __forceinline__ C raw_to_g(C raw, C inv_scale) {
     else return raw;
 }
 
-// Pull the pre-collision populations of nodes x0 .. x0+VEC-1 of row (y, z):
-// f as deviations d_i = f_i - w_i, g as values.
+// Pull the pre-collision populations of nodes x0 .. x0+VEC-1 whose own slot in
+// plane 0 is `own`: f as deviations d_i = f_i - w_i, g as values.
 template <int DIM, class S, int VEC, class C>
-__device__ __forceinline__ void pull_node_vec(const S* __restrict__ src, const KParams& p, int y, int z, int x0ld,
-                                              int lane, C (&f)[Lat<DIM>::F::Q][VEC],
-                                              C (&g)[Lat<DIM>::G::Q][VEC]) {
+__device__ __forceinline__ void pull_node_vec(const S* __restrict__ own, const KParams& p, int lane,
+                                              C (&f)[Lat<DIM>::F::Q][VEC], C (&g)[Lat<DIM>::G::Q][VEC]) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
-    const Layout& L = p.L;
     const C inv_scale = ScaleOf<C>::inv(p);
-    const S* __restrict__ gsrc = src + (long long)LF::Q * L.plane;
     static_for<LF::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        const long long row = L.row(y - LF::e(i, 1), z - LF::e(i, 2));
         C t[VEC];
-        pull_row<S, VEC, LF::e(i, 0), C>(src + (long long)i * L.plane, row, x0ld, lane, t);
+        pull_row<S, VEC, LF::e(i, 0), C>(own + p.loff[i], lane, t);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) f[i][k] = raw_to_dev<LF, S, C>(t[k], i, inv_scale);
     });
     static_for<LG::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        const long long row = L.row(y - LG::e(i, 1), z - LG::e(i, 2));
         C t[VEC];
-        pull_row<S, VEC, LG::e(i, 0), C>(gsrc + (long long)i * L.plane, row, x0ld, lane, t);
+        pull_row<S, VEC, LG::e(i, 0), C>(own + p.loff[LF::Q + i], lane, t);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g<S, C>(t[k], inv_scale);
     });
+}
+
+// Wall and periodic rules for the nodes of a thread at the edge of the cell.
+// Kept out of line: only edge threads call it, and its fully unrolled body
+// would otherwise crowd the instruction cache of the hot path.
+template <int DIM, class S, int VEC, class C>
+__device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, int x0, int y, int z,
+                                         const C* __restrict__ post) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    constexpr int QF = LF::Q, QG = LG::Q;
+    const C scale = ScaleOf<C>::s(p);
+    S* __restrict__ gdst = dst + (long long)QF * p.L.plane;
+    for (int k = 0; k < VEC; ++k) {
+        const int x = x0 + k;
+        if (x >= p.L.nx) break;
+        static_for<QF>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            ghost_write<LF, false, i, S, C>(dst, p, x, y, z, post[i * VEC + k], scale);
+        });
+        static_for<QG>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            ghost_write<LG, true, i, S, C>(gdst, p, x, y, z, post[(QF + i) * VEC + k], scale);
+        });
+    }
 }
 
 // One thread updates VEC consecutive nodes of one row.  blockDim.x must be a
@@ -593,9 +622,10 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
     if (x0 - lane * VEC >= L.nx) return;  // the whole warp lies past the row end
     const int x0ld = min(x0, p.xmax_load);
     const C scale = ScaleOf<C>::s(p);
+    const long long row = L.row(y, z);
 
     C f[QF][VEC], g[QG][VEC];
-    pull_node_vec<DIM, S, VEC, C>(src, p, y, z, x0ld, lane, f, g);
+    pull_node_vec<DIM, S, VEC, C>(src + row + x0ld, p, lane, f, g);
 
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
@@ -612,22 +642,21 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
     }
 
     if (x0 >= L.nx) return;
-    const long long own = L.row(y, z) + x0;
-    S* __restrict__ gdst = dst + (long long)QF * L.plane;
+    S* __restrict__ own = dst + row + x0;
     if (x0 + VEC <= L.nx) {
         static_for<QF>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; ++k) v[k] = enc_f<LF, S, C>(f[i][k], i, scale);
-            st_vec<S, VEC>(dst + (long long)i * L.plane + own, v);
+            st_vec<S, VEC>(own + p.soff[i], v);
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; ++k) v[k] = enc_g<S, C>(g[i][k], scale);
-            st_vec<S, VEC>(gdst + (long long)i * L.plane + own, v);
+            st_vec<S, VEC>(own + p.soff[QF + i], v);
         });
     } else {
 #pragma unroll
@@ -635,11 +664,11 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
             if (x0 + k < L.nx) {
                 static_for<QF>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    dst[(long long)i * L.plane + own + k] = enc_f<LF, S, C>(f[i][k], i, scale);
+                    own[p.soff[i] + k] = enc_f<LF, S, C>(f[i][k], i, scale);
                 });
                 static_for<QG>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    gdst[(long long)i * L.plane + own + k] = enc_g<S, C>(g[i][k], scale);
+                    own[p.soff[QF + i] + k] = enc_g<S, C>(g[i][k], scale);
                 });
             }
         }
@@ -649,20 +678,15 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
     const bool edge = (x0 == 0) || (x0 + VEC >= L.nx) || (y == 0) || (y == L.ny - 1) ||
                       (DIM == 3 && (z == 0 || z == L.nz - 1));
     if (edge) {
+        C post[(QF + QG) * VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
-            const int x = x0 + k;
-            if (x < L.nx) {
-                static_for<QF>([&](auto ii) {
-                    constexpr int i = decltype(ii)::value;
-                    ghost_write<LF, false, i, S, C>(dst, p, x, y, z, f[i][k], scale);
-                });
-                static_for<QG>([&](auto ii) {
-                    constexpr int i = decltype(ii)::value;
-                    ghost_write<LG, true, i, S, C>(gdst, p, x, y, z, g[i][k], scale);
-                });
-            }
+#pragma unroll
+            for (int i = 0; i < QF; ++i) post[i * VEC + k] = f[i][k];
+#pragma unroll
+            for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = g[i][k];
         }
+        edge_writes<DIM, S, VEC, C>(dst, p, x0, y, z, post);
     }
 }
 
