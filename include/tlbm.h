@@ -190,7 +190,17 @@ TLBM_API int tlbm_derived(tlbm_t h, double* out, int cap, int* count);
  * per block (0 = the tuned default of the lattice and precision).  All variants compute the same collision;
  * TLBM_ERR_UNSUPPORTED if the variant is not compiled. */
 TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y);
-/* Current variant (form reported as 1 MRT or 2 TRT).  Outputs may be NULL. */
+/* Use the shared-memory staged step kernel instead: a persistent grid whose
+ * blocks copy each tile's source rows (one row segment of tile_width nodes per
+ * population) into shared memory with TMA bulk copies completing on mbarriers,
+ * `stages` tiles in flight per block (0 = defaults: whole rows in 3D, 512 nodes in
+ * 2D; 4 stages).  FP32/FP16/BF16 storage with two-relaxation-time rates only
+ * (TLBM_ERR_UNSUPPORTED otherwise).  A block that waits too long for its copies
+ * gives up; the next synchronising call then returns TLBM_ERR_TIMEOUT.
+ * tlbm_set_variant switches back to the register kernels. */
+TLBM_API int tlbm_set_staged(tlbm_t h, int tile_width, int stages);
+/* Current variant (form reported as 1 MRT or 2 TRT; vec 0 for the staged
+ * kernel).  Outputs may be NULL. */
 TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y);
 
 /* FP64 diagnostic sums of a population state without any device memory from

@@ -28,6 +28,7 @@ UNITS = {
     "step_3d_f16.cu": [],
     "step_fp64.cu": ["--fmad=false"],
     "noalloc.cu": [],
+    "step_staged.cu": [],
 }
 
 

@@ -542,6 +542,7 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
     h->popset_bytes = align_up((size_t)(h->qf + h->qg) * (size_t)kp.L.plane * h->elem, 256);
     h->red_off = 2 * h->popset_bytes;
     h->res_off = h->red_off + align_up((size_t)RED_BLOCKS * RED_FIELDS * sizeof(double), 256);
+    h->status_off = h->res_off + 128;
     h->stage_off = h->res_off + 256;
     const long long N = (long long)nx * ny * nz;
     h->total_bytes = h->stage_off + align_up((size_t)std::min<long long>(N, STAGE_NODES) * sizeof(double), 256);
@@ -590,6 +591,8 @@ extern "C" int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp) {
     if (!std::isfinite(noise_amp) || noise_amp < 0) return fail(h, TLBM_ERR_ARG, "noise_amp must be finite, >= 0");
     cudaError_t e = cudaMemsetAsync(h->mem, 0, 2 * h->popset_bytes, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    e = cudaMemsetAsync(h->mem + h->status_off, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     h->cur = 0;
     e = with_types(h->dim, h->prec, [&](auto K) { return decltype(K)::init(h->buf[0], h->kp, seed, noise_amp, h->stream); });
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
@@ -600,6 +603,24 @@ extern "C" int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp) {
 
 static cudaError_t launch_one_step(tlbm_t h) {
     const KParams& kp = h->kp;
+    if (h->staged) {
+        const int A = 16 / (int)h->elem;
+        StagedInfo si;
+        si.tw = h->staged_tw;
+        si.tiles_per_row = (h->nx + si.tw - 1) / si.tw;
+        si.tiles = (long long)h->ny * h->nz * si.tiles_per_row;
+        si.lw = si.tw + 2 * A;
+        si.stages = h->staged_stages;
+        si.status = (int*)(h->mem + h->status_off);
+        cudaError_t e = launch_staged(h->dim, h->prec, h->buf[h->cur], h->buf[h->cur ^ 1], kp, si, h->staged_grid,
+                                      h->staged_smem, h->stream);
+        if (e == cudaSuccess) {
+            h->cur ^= 1;
+            h->t += 1;
+            h->launches += 1;
+        }
+        return e;
+    }
     const int vec = h->vec;
     const int bx = h->bx, by = h->by;
     const int threads_x = (h->nx + vec - 1) / vec;
@@ -651,8 +672,12 @@ static int run_reduce(tlbm_t h, double* res) {
     h->launches += 2;
     e = cudaMemcpyAsync(res, out, RED_FIELDS * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
+    int status = 0;
+    e = cudaMemcpyAsync(&status, h->mem + h->status_off, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    if (status) return fail(h, TLBM_ERR_TIMEOUT, "a staged step gave up waiting for its copies");
     return TLBM_OK;
 }
 
@@ -788,13 +813,50 @@ extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bl
     h->trt = trt;
     h->bx = bx;
     h->by = by;
+    h->staged = 0;
     h->kp.xmax_load = h->kp.L.P - v;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_set_staged(tlbm_t h, int tile_width, int stages) {
+    TLBM_CHECK_HANDLE(h);
+    if (h->prec == TLBM_FP64) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel has no FP64 variant");
+    if (!h->kp.trt) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel needs two-relaxation-time rates");
+    const int A = 16 / (int)h->elem;
+    int tw = tile_width > 0 ? tile_width : (h->dim == 3 ? (h->nx + A - 1) / A * A : 512);
+    if (tw % A || tw < A || tw > 4096)
+        return fail(h, TLBM_ERR_ARG, "tile_width must be a multiple of %d in [%d, 4096]", A, A);
+    const int ns = stages > 0 ? stages : 4;
+    if (ns < 2 || ns > STAGED_MAX_STAGES) return fail(h, TLBM_ERR_ARG, "stages must be in [2, %d]", STAGED_MAX_STAGES);
+    const size_t smem = 128 + (size_t)ns * (h->qf + h->qg) * (size_t)(tw + 2 * A) * h->elem;
+    const void* fn = staged_function(h->dim, h->prec);
+    if (!fn) return fail(h, TLBM_ERR_UNSUPPORTED, "staged kernel not built for this precision");
+    // allow the device's full opt-in shared memory for this kernel, so that
+    // handles with different tile shapes can share it
+    int dev = 0, optin = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
+    if (smem > (size_t)optin) return fail(h, TLBM_ERR_ARG, "%zu bytes of shared memory per block exceed %d", smem, optin);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute (shared memory size)");
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, STAGED_THREADS, smem);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(h, TLBM_ERR_ARG, "%zu bytes of shared memory per block do not fit", smem);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
+    const long long tiles = (long long)h->ny * h->nz * ((h->nx + tw - 1) / tw);
+    h->staged = 1;
+    h->staged_tw = tw;
+    h->staged_stages = ns;
+    h->staged_smem = smem;
+    h->staged_grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
     return TLBM_OK;
 }
 
 extern "C" int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y) {
     TLBM_CHECK_HANDLE(h);
-    if (vec) *vec = h->vec;
+    if (vec) *vec = h->staged ? 0 : h->vec;
     if (form) *form = h->trt ? 2 : 1;
     if (block_x) *block_x = h->bx;
     if (block_y) *block_y = h->by;

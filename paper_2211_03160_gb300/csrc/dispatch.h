@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "staged.cuh"
 
 namespace tlbm {
 
@@ -16,6 +17,11 @@ cudaError_t launch_step(int dim, int prec, int vec, bool trt, const void* src, v
 bool step_variant_available(int dim, int prec, int vec, bool trt);
 // device function of a compiled variant (for cudaFuncGetAttributes), or nullptr
 const void* step_function(int dim, int prec, int vec, bool trt);
+
+// shared-memory staged (TMA bulk copy) step, TRT form, FP32/FP16/BF16 storage
+const void* staged_function(int dim, int prec);
+cudaError_t launch_staged(int dim, int prec, const void* src, void* dst, const KParams& p, const StagedInfo& si,
+                          int grid, size_t smem, cudaStream_t s);
 
 // per-unit entry points
 cudaError_t launch_step_2d_f32(int vec, bool trt, const void*, void*, const KParams&, dim3, dim3, cudaStream_t);

@@ -15,9 +15,13 @@ struct tlbm_s {
     double S[tlbm::MAXQ], Q[7];
     tlbm::KParams kp;
     int vec, trt, bx, by;      // step kernel variant and block shape
+    int staged;                // 1: shared-memory staged (TMA bulk copy) kernel
+    int staged_tw, staged_stages, staged_grid;
+    size_t staged_smem;
     size_t elem;               // bytes per stored value
     size_t popset_bytes;       // one population buffer (f planes then g planes)
     size_t red_off, res_off, stage_off, total_bytes;
+    size_t status_off;         // device status word of the staged kernel
     char* mem;                 // bound device block
     size_t mem_bytes;
     void* buf[2];

@@ -80,6 +80,7 @@ _SIGS = {
     "tlbm_get_variant": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int)]),
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "tlbm_last_error": (C.c_char_p, [C.c_void_p]),
     "tlbm_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "tlbm_destroy": (None, [C.c_void_p]),
@@ -214,6 +215,10 @@ def tlbm_derived(h) -> list:
 
 def tlbm_set_variant(h, vec=0, form=0, block_x=0, block_y=0):
     _check(h, lib().tlbm_set_variant(h, int(vec), int(form), int(block_x), int(block_y)))
+
+
+def tlbm_set_staged(h, tile_width=0, stages=0):
+    _check(h, lib().tlbm_set_staged(h, int(tile_width), int(stages)))
 
 
 def tlbm_get_variant(h):
@@ -351,6 +356,9 @@ class Sim:
 
     def set_variant(self, vec=0, form=0, block_x=0, block_y=0):
         tlbm_set_variant(self.h, vec, form, block_x, block_y)
+
+    def set_staged(self, tile_width=0, stages=0):
+        tlbm_set_staged(self.h, tile_width, stages)
 
     @property
     def variant(self):

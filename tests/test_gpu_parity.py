@@ -113,10 +113,19 @@ def test_one_step_random_populations(T, O, prec, lattice, shape, walls, pm):
     f = inputs.uniform_array(seed, (qf,) + o.shape, 0.02, 0.2)
     gg = inputs.uniform_array(seed + 1, (qg,) + o.shape, -0.1, 0.1)
     ref = None
-    for vec, form in VARIANTS[(lattice, prec)]:
+    variants = list(VARIANTS[(lattice, prec)])
+    if prec != FP64:
+        # shared-memory staged kernel: several tiles per row, 2 and 3 stages
+        A = 16 // (4 if prec == FP32 else 2)
+        variants += [("staged", A, 2), ("staged", 2 * A, 3)]
+    for vec, form, *st in variants:
         g = T.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec, **kw)
-        g.set_variant(vec, form)
-        assert g.variant[:2] == (vec, form)
+        if vec == "staged":
+            g.set_staged(form, st[0])
+            assert g.variant[0] == 0
+        else:
+            g.set_variant(vec, form)
+            assert g.variant[:2] == (vec, form)
         g.set_populations(f, gg)
         f0, g0 = g.get_populations()  # as stored in the GPU precision
         if ref is None:
@@ -135,8 +144,8 @@ def test_one_step_random_populations(T, O, prec, lattice, shape, walls, pm):
 
 
 def test_variants_agree_bitwise(T):
-    """Nodes per thread and block shape change only how loads are issued: the
-    TRT variants give bit-identical states, and so do the MRT variants."""
+    """Nodes per thread, block shape and the shared-memory staged kernel change
+    only how loads are issued: all TRT variants give bit-identical states."""
     for lattice, shape, prec in ((D2, (301, 45, 1), FP32), (D2, (301, 45, 1), FP16), (D3, (77, 21, 13), FP32),
                                  (D3, (77, 21, 13), BF16)):
         outs = []
@@ -148,6 +157,13 @@ def test_variants_agree_bitwise(T):
                 g.step(20)
                 outs.append(g.get_populations())
                 g.close()
+        for tw, ns in ((0, 0), (16, 2), (64, 5)):
+            g = T.Sim(*shape, lattice=lattice, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
+            g.set_staged(tw, ns)
+            g.init(11, 1e-3)
+            g.step(20)
+            outs.append(g.get_populations())
+            g.close()
         for f, gg in outs[1:]:
             assert np.array_equal(f, outs[0][0]) and np.array_equal(gg, outs[0][1])
 
@@ -250,6 +266,23 @@ def test_divergence_is_reported(T):
     assert div
     g.init(1, 1e-3)
     assert not g.status()[0]
+
+
+def test_staged_at_bench_size(T):
+    """The staged kernel on the 385^3 FP16 cube agrees bitwise with the register
+    kernel after a few steps (whole-row tiles, the staged default in 3D)."""
+    outs = []
+    for staged in (False, True):
+        g = T.Sim(385, 385, 385, lattice=D3, Ra=1e7, Pr=0.71, Ma=0.1, precision=FP16)
+        if staged:
+            g.set_staged()
+        g.init(3, 1e-3)
+        g.step(4)
+        outs.append(g.get_window(180, 0, 0, 24, 24, 24))
+        outs.append(g.get_window(361, 361, 361, 24, 24, 24))
+        assert not g.status()[0]
+        g.close()
+    assert all(np.array_equal(a, b) for a, b in zip(outs[0] + outs[1], outs[2] + outs[3]))
 
 
 def test_launch_count(T):
