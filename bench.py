@@ -260,6 +260,75 @@ def run_gpu(name: str, steps: int, warmup: int, ws: int, device_index: int, e2e:
     return out
 
 
+def ensemble_draws(n: int = 64, master_seed: int = 4):
+    """64-instance ensemble: square cells with N uniform in {129, 257, 513, 1025},
+    log10 Ra uniform in [5, 8], Pr in {0.71, 7.0}, seeds 1000 + i."""
+    import numpy as np
+
+    r = np.random.default_rng(master_seed)
+    out = []
+    for i in range(n):
+        N = int(r.choice([129, 257, 513, 1025]))
+        Ra = float(10.0 ** r.uniform(5.0, 8.0))
+        Pr = float(r.choice([0.71, 7.0]))
+        out.append((N, N, 1, Ra, Pr, 0.1, 1000 + i))
+    return out
+
+
+def run_batch(prec: str, steps: int, warmup: int, ws: int, device_index: int) -> dict:
+    """The ensemble stepped by one flattened launch per step (CUDA-graph step
+    blocks) against the same 64 cells stepped by 64 separate launches per step."""
+    import torch
+
+    from paper_2211_03160_gb300 import tlbm
+
+    inst = ensemble_draws()
+    nodes = sum(nx * ny for nx, ny, *_ in inst)
+    stream = torch.cuda.Stream()
+    out = {"instances": len(inst), "nodes": nodes, "prec": prec}
+    with torch.cuda.stream(stream):
+        b = tlbm.Batch(inst, lattice=tlbm.TLBM_D2Q9_D2Q5, precision=tlbm.PRECISIONS[prec], stream=stream)
+        b.init(1e-3)
+        b.autotune(3)
+        b.step(warmup)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        torch.cuda.synchronize()
+        l0 = b.launches
+        ev0.record(stream)
+        b.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        out["batched"] = {"sec": max_over_ranks(sec, ws, torch.device("cuda", device_index) if ws > 1 else None),
+                          "launches": b.launches - l0, "variant": list(b.variant),
+                          "diverged": sum(b.status())}
+        b.close()
+        sims = [tlbm.Sim(nx, ny, nz, lattice=tlbm.TLBM_D2Q9_D2Q5, Ra=Ra, Pr=Pr, Ma=Ma,
+                         precision=tlbm.PRECISIONS[prec], stream=stream) for nx, ny, nz, Ra, Pr, Ma, _ in inst]
+        for s, (*_, seed) in zip(sims, inst):
+            s.init(seed, 1e-3)
+        for _ in range(warmup):
+            for s in sims:
+                s.step(1)
+        barrier(ws)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            for s in sims:
+                s.step(1)
+        ev1.record(stream)
+        ev1.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        out["separate"] = {"sec": max_over_ranks(sec, ws, torch.device("cuda", device_index) if ws > 1 else None),
+                           "launches": steps * len(sims)}
+        for s in sims:
+            s.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(target_seconds: float = 12.0) -> dict:
     """The FP64 oracle as it stands on the host cores (OpenMP over all cores),
     on a bounded sample of the headline workload: the same physics (Ra = 1e8,
@@ -327,7 +396,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d_8193_fp32")
-    ap.add_argument("--variants", default="2d_8193_fp16,2d_8193_bf16,3d_385_fp32,3d_385_fp16,2d_8193_fp64")
+    ap.add_argument("--variants", default="2d_8193_fp16,2d_8193_bf16,3d_385_fp32,3d_385_fp16,2d_8193_fp64,"
+                                          "batch64_fp32,batch64_fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -350,6 +420,21 @@ def main():
     main_run = run_gpu(args.workload, args.steps, args.warmup, ws, local, e2e=not args.no_e2e)
     variants = {}
     for v in [x for x in args.variants.split(",") if x]:
+        if v.startswith("batch64_"):
+            st = max(10, args.steps // 4)
+            r = run_batch(v.split("_")[1], st, min(args.warmup, 20), ws, local)
+            bt, sp = r["batched"], r["separate"]
+            variants[v] = {
+                "workload": (f"64-instance 2D RB ensemble, N in {{129,257,513,1025}}, log10 Ra in [5,8], "
+                             f"Pr in {{0.71,7}}, {r['prec'].upper()} storage, {r['nodes']} nodes"),
+                "steps": st, "unit": "GLUPS",
+                "value": r["nodes"] * ws * st / bt["sec"] / 1e9,
+                "separate_launches_value": r["nodes"] * ws * st / sp["sec"] / 1e9,
+                "speedup_vs_separate": sp["sec"] / bt["sec"],
+                "batched_launches": bt["launches"], "separate_launches": sp["launches"],
+                "variant": bt["variant"], "diverged_instances": bt["diverged"],
+            }
+            continue
         st = args.steps if not v.endswith("fp64") else max(10, args.steps // 10)
         if v.startswith("3d"):
             st = max(10, st // 2)

@@ -203,6 +203,49 @@ TLBM_API int tlbm_set_staged(tlbm_t h, int tile_width, int stages);
  * kernel).  Outputs may be NULL. */
 TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y);
 
+/* ---------------------------------------------------------------- batched ensemble
+ * n independent cells with their own sizes, (Ra, Pr, Ma) and seeds, one lattice
+ * and precision.  One flattened launch advances every instance by one step;
+ * blocks of graph_steps steps are replayed as one CUDA graph launch.  Each
+ * instance is an ordinary handle bound to its own slice of the batch's block
+ * (tlbm_batch_instance), so the single-cell calls (macros, populations,
+ * reductions) apply to it; it must not be destroyed, re-bound or stepped on its
+ * own.  Errors as for the single-cell calls, text in tlbm_batch_last_error. */
+typedef struct tlbm_batch_s* tlbm_batch_t;
+
+/* Create (host memory only).  p applies to every instance (NULL = defaults). */
+TLBM_API int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* instances, int lattice,
+                               int precision, const tlbm_params* p);
+/* Device bytes for all instances plus the launch tables, 256-byte aligned. */
+TLBM_API int tlbm_batch_required_bytes(tlbm_batch_t b, size_t* bytes);
+/* Bind a caller-owned, 256-byte aligned device block (never freed by the library). */
+TLBM_API int tlbm_batch_bind_memory(tlbm_batch_t b, void* dev_ptr, size_t bytes);
+TLBM_API int tlbm_batch_set_stream(tlbm_batch_t b, void* cuda_stream);
+/* tlbm_init of every instance with its own tlbm_instance.seed. */
+TLBM_API int tlbm_batch_init(tlbm_batch_t b, double noise_amp);
+/* Advance every instance by n steps.  Asynchronous. */
+TLBM_API int tlbm_batch_step(tlbm_batch_t b, int64_t n);
+/* Launch shape of the batched kernel (0 keeps the current value; form as in
+ * tlbm_set_variant) and the steps per graph launch (even; 0 = no graph). */
+TLBM_API int tlbm_batch_set_variant(tlbm_batch_t b, int vec, int form, int block_x, int block_y,
+                                    int graph_steps);
+TLBM_API int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* block_x, int* block_y,
+                                    int* graph_steps);
+/* Time the compiled launch shapes (trials launches each) on the bound state and
+ * keep the fastest.  The state is not changed. */
+TLBM_API int tlbm_batch_autotune(tlbm_batch_t b, int trials);
+/* Borrow instance idx as a single-cell handle (owned by the batch). */
+TLBM_API int tlbm_batch_instance(tlbm_batch_t b, int idx, tlbm_t* out);
+/* Per-instance Nusselt numbers / divergence flags into nu[n] / diverged[n]. */
+TLBM_API int tlbm_batch_nusselt(tlbm_batch_t b, double* nu);
+TLBM_API int tlbm_batch_status(tlbm_batch_t b, int* diverged);
+/* tlbm_macros of instance idx. */
+TLBM_API int tlbm_batch_macros(tlbm_batch_t b, int idx, void* rho, void* ux, void* uy, void* uz, void* T,
+                               int out_dtype);
+TLBM_API int tlbm_batch_launch_count(tlbm_batch_t b, int64_t* count);
+TLBM_API const char* tlbm_batch_last_error(tlbm_batch_t b);
+TLBM_API void tlbm_batch_destroy(tlbm_batch_t b);
+
 /* FP64 diagnostic sums of a population state without any device memory from
  * the caller beyond the state itself (the paper has no counterpart; this is a
  * library service).  For callers that hold a state but cannot allocate device

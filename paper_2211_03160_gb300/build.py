@@ -29,6 +29,7 @@ UNITS = {
     "step_fp64.cu": ["--fmad=false"],
     "noalloc.cu": [],
     "step_staged.cu": [],
+    "batch.cu": [],
 }
 
 

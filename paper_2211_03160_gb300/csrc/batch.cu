@@ -1,0 +1,487 @@
+// Batched ensemble of independent cells (same lattice and storage, own sizes,
+// Rayleigh and Prandtl numbers and seeds): one flattened launch steps every
+// instance, captured into a CUDA graph of `graph_steps` steps so that a block
+// of steps costs one graph launch.  Each instance is an ordinary handle bound to
+// its own slice of the batch's device block, so every single-cell call
+// (macros, populations, reductions) works on it unchanged.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/tlbm.h"
+#include "dispatch.h"
+#include "handle.h"
+
+using namespace tlbm;
+
+namespace {
+
+struct BatchInst {
+    const void* buf[2];  // population buffers of the instance
+    long long block0;    // first flattened block of the instance
+    int gx, gy;          // blocks along x and y of the instance (z: nz)
+};
+
+// Block b of the flattened grid belongs to the instance i with
+// block0[i] <= b < block0[i+1]; its parameters are staged in shared memory.
+template <int DIM, class S, int VEC, bool TRT>
+__global__ void batch_step_kernel(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
+                                  int parity) {
+    __shared__ KParams sp;
+    __shared__ int si;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y;
+    if (tid == 0) {
+        int lo = 0, hi = n - 1;
+        const long long b = blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (inst[mid].block0 <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        si = lo;
+    }
+    __syncthreads();
+    const int i = si;
+    {
+        const int* src = reinterpret_cast<const int*>(kps + i);
+        int* dst = reinterpret_cast<int*>(&sp);
+        for (int w = tid; w < (int)(sizeof(KParams) / sizeof(int)); w += nt) dst[w] = src[w];
+    }
+    __syncthreads();
+    const BatchInst in = inst[i];
+    const long long local = (long long)blockIdx.x - in.block0;
+    const int bx = (int)(local % in.gx);
+    const long long r = local / in.gx;
+    const int by = (int)(r % in.gy);
+    const int bz = (int)(r / in.gy);
+    step_block<DIM, S, VEC, TRT>((const S*)in.buf[parity], (S*)in.buf[parity ^ 1], sp, bx, by, bz);
+}
+
+#define TLBM_BATCH_CASE(DIM, S, PREC, VEC, TRT)                                                      \
+    if (dim == DIM && prec == PREC && vec == VEC && trt == TRT) {                                   \
+        if (launch)                                                                                 \
+            batch_step_kernel<DIM, S, VEC, TRT><<<grid, block, 0, s>>>(kps, inst, n, parity);       \
+        return launch ? cudaGetLastError() : cudaSuccess;                                           \
+    }
+
+cudaError_t batch_dispatch(bool launch, int dim, int prec, int vec, bool trt, const KParams* kps,
+                           const BatchInst* inst, int n, int parity, long long grid, dim3 block, cudaStream_t s) {
+    TLBM_BATCH_CASE(2, float, 1, 4, true)
+    TLBM_BATCH_CASE(2, float, 1, 2, true)
+    TLBM_BATCH_CASE(2, float, 1, 4, false)
+    TLBM_BATCH_CASE(2, __half, 2, 4, true)
+    TLBM_BATCH_CASE(2, __half, 2, 8, true)
+    TLBM_BATCH_CASE(2, __half, 2, 8, false)
+    TLBM_BATCH_CASE(2, __nv_bfloat16, 3, 4, true)
+    TLBM_BATCH_CASE(2, __nv_bfloat16, 3, 8, true)
+    TLBM_BATCH_CASE(2, __nv_bfloat16, 3, 8, false)
+    TLBM_BATCH_CASE(2, double, 0, 2, true)
+    TLBM_BATCH_CASE(2, double, 0, 2, false)
+    TLBM_BATCH_CASE(3, float, 1, 2, true)
+    TLBM_BATCH_CASE(3, float, 1, 1, true)
+    TLBM_BATCH_CASE(3, float, 1, 2, false)
+    TLBM_BATCH_CASE(3, __half, 2, 1, true)
+    TLBM_BATCH_CASE(3, __half, 2, 4, false)
+    TLBM_BATCH_CASE(3, __nv_bfloat16, 3, 1, true)
+    TLBM_BATCH_CASE(3, __nv_bfloat16, 3, 4, false)
+    TLBM_BATCH_CASE(3, double, 0, 1, true)
+    TLBM_BATCH_CASE(3, double, 0, 1, false)
+    return cudaErrorInvalidValue;
+}
+
+thread_local char g_batch_create_error[256] = "";
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct tlbm_batch_s {
+    int n, dim, lattice, prec;
+    std::vector<tlbm_t> inst;
+    std::vector<size_t> off;      // byte offset of each instance's slice
+    std::vector<uint64_t> seeds;  // per-instance initial-state seeds
+    size_t tables_off, total_bytes;
+    char* mem;
+    size_t mem_bytes;
+    KParams* d_kp;
+    BatchInst* d_inst;
+    int vec, trt, bx, by;
+    int graph_steps;
+    long long total_blocks;
+    int parity;
+    int64_t t;
+    cudaStream_t stream;
+    cudaStream_t capture_stream;
+    cudaGraphExec_t graph;
+    int64_t launches;
+    char err[256];
+};
+
+static int bfail(tlbm_batch_t b, int code, const char* fmt, ...) {
+    char* dst = b ? b->err : g_batch_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static void drop_graph(tlbm_batch_t b) {
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+// default variant: the tuned single-cell one (see api.cu), restricted to the
+// batch's compiled set
+static void batch_default_variant(tlbm_batch_t b) {
+    int v = 0, form = 0, bx = 0, by = 0;
+    tlbm_get_variant(b->inst[0], &v, &form, &bx, &by);
+    b->vec = v;
+    b->trt = 1;
+    for (tlbm_t h : b->inst) b->trt = b->trt && h->kp.trt;
+    b->bx = bx;
+    b->by = by;
+    if (batch_dispatch(false, b->dim, b->prec, b->vec, b->trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr) !=
+        cudaSuccess) {
+        // fall back to the batch's first compiled vector width for this storage
+        const int cand[] = {4, 8, 2, 1};
+        for (int c : cand)
+            if (batch_dispatch(false, b->dim, b->prec, c, b->trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr) ==
+                cudaSuccess) {
+                b->vec = c;
+                break;
+            }
+    }
+}
+
+// per-instance tables for the flattened launch (host side)
+static void build_tables(tlbm_batch_t b, std::vector<KParams>& kps, std::vector<BatchInst>& ins) {
+    kps.resize(b->n);
+    ins.resize(b->n);
+    long long block0 = 0;
+    for (int i = 0; i < b->n; ++i) {
+        tlbm_t h = b->inst[i];
+        kps[i] = h->kp;
+        kps[i].xmax_load = h->kp.L.P - b->vec;
+        const int tx = (h->nx + b->vec - 1) / b->vec;
+        const int gx = (tx + b->bx - 1) / b->bx;
+        const int gy = (h->ny + b->by - 1) / b->by;
+        ins[i].buf[0] = h->buf[0];
+        ins[i].buf[1] = h->buf[1];
+        ins[i].block0 = block0;
+        ins[i].gx = gx;
+        ins[i].gy = gy;
+        block0 += (long long)gx * gy * h->nz;
+    }
+    b->total_blocks = block0;
+}
+
+static int upload_tables(tlbm_batch_t b) {
+    std::vector<KParams> kps;
+    std::vector<BatchInst> ins;
+    build_tables(b, kps, ins);
+    cudaError_t e = cudaMemcpyAsync(b->d_kp, kps.data(), sizeof(KParams) * b->n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_inst, ins.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+    drop_graph(b);
+    return TLBM_OK;
+}
+
+static cudaError_t launch_batch(tlbm_batch_t b, int parity, cudaStream_t s) {
+    return batch_dispatch(true, b->dim, b->prec, b->vec, b->trt != 0, b->d_kp, b->d_inst, b->n, parity,
+                          b->total_blocks, dim3(b->bx, b->by, 1), s);
+}
+
+extern "C" int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* instances, int lattice,
+                                 int precision, const tlbm_params* p) {
+    g_batch_create_error[0] = 0;
+    if (!out) return bfail(nullptr, TLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 65536 || !instances) return bfail(nullptr, TLBM_ERR_ARG, "need 1..65536 instances");
+    tlbm_batch_s* b = new (std::nothrow) tlbm_batch_s();
+    if (!b) return bfail(nullptr, TLBM_ERR_OOM, "host allocation failed");
+    b->n = n;
+    b->lattice = lattice;
+    b->prec = precision;
+    b->dim = lattice == TLBM_D3Q19_D3Q7 ? 3 : 2;
+    b->graph_steps = 16;
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        tlbm_t h = nullptr;
+        const tlbm_instance& in = instances[i];
+        int rc = tlbm_create(&h, in.nx, in.ny, in.nz, lattice, in.Ra, in.Pr, in.Ma, precision, p);
+        if (rc != TLBM_OK) {
+            bfail(nullptr, rc, "instance %d: %s", i, tlbm_last_error(nullptr));
+            for (tlbm_t q : b->inst) tlbm_destroy(q);
+            delete b;
+            return rc;
+        }
+        b->inst.push_back(h);
+        b->off.push_back(off);
+        b->seeds.push_back(in.seed);
+        size_t need = 0;
+        tlbm_required_bytes(h, &need);
+        off += align_up(need, 256);
+    }
+    b->tables_off = off;
+    b->total_bytes = off + align_up(sizeof(KParams) * n, 256) + align_up(sizeof(BatchInst) * n, 256);
+    batch_default_variant(b);
+    *out = b;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_required_bytes(tlbm_batch_t b, size_t* bytes) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!bytes) return bfail(b, TLBM_ERR_ARG, "bytes is NULL");
+    *bytes = b->total_bytes;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_bind_memory(tlbm_batch_t b, void* dev_ptr, size_t bytes) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!dev_ptr || ((uintptr_t)dev_ptr) % 256) return bfail(b, TLBM_ERR_ARG, "dev_ptr must be 256-byte aligned");
+    if (bytes < b->total_bytes) return bfail(b, TLBM_ERR_OOM, "%zu bytes bound, %zu needed", bytes, b->total_bytes);
+    for (int i = 0; i < b->n; ++i) {
+        size_t need = 0;
+        tlbm_required_bytes(b->inst[i], &need);
+        int rc = tlbm_bind_memory(b->inst[i], (char*)dev_ptr + b->off[i], need);
+        if (rc != TLBM_OK) return bfail(b, rc, "instance %d: %s", i, tlbm_last_error(b->inst[i]));
+    }
+    b->mem = (char*)dev_ptr;
+    b->mem_bytes = bytes;
+    b->d_kp = (KParams*)(b->mem + b->tables_off);
+    b->d_inst = (BatchInst*)(b->mem + b->tables_off + align_up(sizeof(KParams) * b->n, 256));
+    b->parity = 0;
+    return upload_tables(b);
+}
+
+extern "C" int tlbm_batch_set_stream(tlbm_batch_t b, void* s) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    b->stream = (cudaStream_t)s;
+    for (tlbm_t h : b->inst) tlbm_set_stream(h, s);
+    drop_graph(b);
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_init(tlbm_batch_t b, double noise_amp) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!b->mem) return bfail(b, TLBM_ERR_UNBOUND, "device memory not bound");
+    for (int i = 0; i < b->n; ++i) {
+        int rc = tlbm_init(b->inst[i], b->seeds[i], noise_amp);
+        if (rc != TLBM_OK) return bfail(b, rc, "instance %d: %s", i, tlbm_last_error(b->inst[i]));
+    }
+    b->parity = 0;
+    b->t = 0;
+    return TLBM_OK;
+}
+
+static void advance(tlbm_batch_t b, int64_t k) {
+    for (tlbm_t h : b->inst) {
+        h->cur = (int)((h->cur + k) & 1);
+        h->t += k;
+    }
+    b->parity = (int)((b->parity + k) & 1);
+    b->t += k;
+}
+
+static int build_graph(tlbm_batch_t b) {
+    drop_graph(b);
+    cudaError_t e = cudaSuccess;
+    if (!b->capture_stream) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < b->graph_steps && le == cudaSuccess; ++k) le = launch_batch(b, k & 1, b->capture_stream);
+    e = cudaStreamEndCapture(b->capture_stream, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(b, TLBM_ERR_CUDA, "capture: %s", cudaGetErrorString(le != cudaSuccess ? le : e));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return bfail(b, TLBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_step(tlbm_batch_t b, int64_t n) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!b->mem) return bfail(b, TLBM_ERR_UNBOUND, "device memory not bound");
+    if (n < 0) return bfail(b, TLBM_ERR_ARG, "n must be >= 0");
+    while (n > 0) {
+        if (b->graph_steps >= 2 && b->parity == 0 && n >= b->graph_steps) {
+            if (!b->graph) {
+                int rc = build_graph(b);
+                if (rc != TLBM_OK) return rc;
+            }
+            cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+            advance(b, b->graph_steps);
+            b->launches += b->graph_steps;
+            n -= b->graph_steps;
+        } else {
+            cudaError_t e = launch_batch(b, b->parity, b->stream);
+            if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "batch step: %s", cudaGetErrorString(e));
+            advance(b, 1);
+            b->launches += 1;
+            n -= 1;
+        }
+    }
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_set_variant(tlbm_batch_t b, int vec, int form, int block_x, int block_y,
+                                      int graph_steps) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    int all_trt = 1;
+    for (tlbm_t h : b->inst) all_trt = all_trt && h->kp.trt;
+    if (form == 2 && !all_trt) return bfail(b, TLBM_ERR_ARG, "not every instance has two-relaxation-time rates");
+    const int trt = form == 1 ? 0 : all_trt;
+    const int v = vec > 0 ? vec : b->vec;
+    const int bx = block_x > 0 ? block_x : b->bx, by = block_y > 0 ? block_y : b->by;
+    if (bx % 32 || bx * by > 1024) return bfail(b, TLBM_ERR_ARG, "block_x must be a multiple of 32, bx*by <= 1024");
+    if (graph_steps < 0 || graph_steps % 2) return bfail(b, TLBM_ERR_ARG, "graph_steps must be even (0 = no graph)");
+    if (batch_dispatch(false, b->dim, b->prec, v, trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr) != cudaSuccess)
+        return bfail(b, TLBM_ERR_UNSUPPORTED, "batch variant (vec %d, %s) not built", v, trt ? "TRT" : "MRT");
+    b->vec = v;
+    b->trt = trt;
+    b->bx = bx;
+    b->by = by;
+    b->graph_steps = graph_steps;
+    if (b->mem) return upload_tables(b);
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* block_x, int* block_y,
+                                      int* graph_steps) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (vec) *vec = b->vec;
+    if (form) *form = b->trt ? 2 : 1;
+    if (block_x) *block_x = b->bx;
+    if (block_y) *block_y = b->by;
+    if (graph_steps) *graph_steps = b->graph_steps;
+    return TLBM_OK;
+}
+
+// Time each candidate launch shape on the bound state without changing it
+// (every trial step reads the current buffers and writes the other ones, and
+// the current buffers stay current), keep the fastest.
+extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!b->mem) return bfail(b, TLBM_ERR_UNBOUND, "device memory not bound");
+    const int reps = trials > 0 ? trials : 5;
+    const int vecs[] = {8, 4, 2, 1};
+    const int shapes[][2] = {{32, 1}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}};
+    const int keep_vec = b->vec, keep_bx = b->bx, keep_by = b->by;
+    float best = 1e30f;
+    int bv = keep_vec, bbx = keep_bx, bby = keep_by;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(b, TLBM_ERR_CUDA, "cudaEventCreate");
+    int rc = TLBM_OK;
+    for (int v : vecs) {
+        if (batch_dispatch(false, b->dim, b->prec, v, b->trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr) !=
+            cudaSuccess)
+            continue;
+        for (const auto& sh : shapes) {
+            b->vec = v;
+            b->bx = sh[0];
+            b->by = sh[1];
+            if ((rc = upload_tables(b)) != TLBM_OK) break;
+            cudaError_t e = launch_batch(b, b->parity, b->stream);  // warm
+            cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_batch(b, b->parity, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                // a shape the kernel cannot launch (resources): skip it
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            b->launches += reps + 1;
+            if (ms < best) {
+                best = ms;
+                bv = v;
+                bbx = sh[0];
+                bby = sh[1];
+            }
+        }
+        if (rc != TLBM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->vec = bv;
+    b->bx = bbx;
+    b->by = bby;
+    int rc2 = upload_tables(b);
+    return rc != TLBM_OK ? rc : rc2;
+}
+
+extern "C" int tlbm_batch_instance(tlbm_batch_t b, int idx, tlbm_t* out) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (idx < 0 || idx >= b->n || !out) return bfail(b, TLBM_ERR_ARG, "bad instance index");
+    *out = b->inst[idx];
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_nusselt(tlbm_batch_t b, double* nu) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!nu) return bfail(b, TLBM_ERR_ARG, "nu is NULL");
+    for (int i = 0; i < b->n; ++i) {
+        int rc = tlbm_nusselt(b->inst[i], &nu[i]);
+        if (rc != TLBM_OK) return bfail(b, rc, "instance %d: %s", i, tlbm_last_error(b->inst[i]));
+    }
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_status(tlbm_batch_t b, int* diverged) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!diverged) return bfail(b, TLBM_ERR_ARG, "diverged is NULL");
+    for (int i = 0; i < b->n; ++i) {
+        int rc = tlbm_status(b->inst[i], &diverged[i], nullptr);
+        if (rc != TLBM_OK) return bfail(b, rc, "instance %d: %s", i, tlbm_last_error(b->inst[i]));
+    }
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_macros(tlbm_batch_t b, int idx, void* rho, void* ux, void* uy, void* uz, void* T,
+                                 int out_dtype) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (idx < 0 || idx >= b->n) return bfail(b, TLBM_ERR_ARG, "bad instance index");
+    int rc = tlbm_macros(b->inst[idx], rho, ux, uy, uz, T, out_dtype);
+    if (rc != TLBM_OK) return bfail(b, rc, "instance %d: %s", idx, tlbm_last_error(b->inst[idx]));
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_launch_count(tlbm_batch_t b, int64_t* count) {
+    if (!b || !count) return bfail(b, TLBM_ERR_ARG, "NULL argument");
+    *count = b->launches;
+    return TLBM_OK;
+}
+
+extern "C" const char* tlbm_batch_last_error(tlbm_batch_t b) { return b ? b->err : g_batch_create_error; }
+
+extern "C" void tlbm_batch_destroy(tlbm_batch_t b) {
+    if (!b) return;
+    drop_graph(b);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (tlbm_t h : b->inst) tlbm_destroy(h);
+    delete b;
+}

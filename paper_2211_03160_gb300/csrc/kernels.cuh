@@ -607,18 +607,20 @@ __device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, 
 
 // One thread updates VEC consecutive nodes of one row.  blockDim.x must be a
 // multiple of 32 so that a warp covers 32*VEC consecutive nodes of one row.
+// Body of the step for the block at grid position (bx, by, bz) of one cell.
 template <int DIM, class S, int VEC, bool TRT>
-__global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
+__device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restrict__ dst, const KParams& p, int bx,
+                                           int by, int bz) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
     using C = typename Storage<S>::C;
     constexpr int QF = LF::Q, QG = LG::Q;
     const Layout& L = p.L;
     const int lane = threadIdx.x & 31;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = DIM == 3 ? (int)blockIdx.z : 0;
+    const int y = by * blockDim.y + threadIdx.y;
+    const int z = DIM == 3 ? bz : 0;
     if (y >= L.ny) return;  // uniform across the warp
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
+    const int x0 = (bx * blockDim.x + threadIdx.x) * VEC;
     if (x0 - lane * VEC >= L.nx) return;  // the whole warp lies past the row end
     const int x0ld = min(x0, p.xmax_load);
     const C scale = ScaleOf<C>::s(p);
@@ -688,6 +690,11 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
         }
         edge_writes<DIM, S, VEC, C>(dst, p, x0, y, z, post);
     }
+}
+
+template <int DIM, class S, int VEC, bool TRT>
+__global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
+    step_block<DIM, S, VEC, TRT>(src, dst, p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ------------------------------------------------------------------ diagnostics

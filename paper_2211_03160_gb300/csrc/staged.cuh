@@ -16,7 +16,8 @@
 
 namespace tlbm {
 
-constexpr int STAGED_THREADS = 128;
+constexpr int STAGED_THREADS = 256;
+constexpr int STAGED_MIN_BLOCKS = 4;  // 64 registers per thread, 32 warps per SM
 constexpr int STAGED_MAX_STAGES = 8;
 constexpr unsigned STAGED_WAIT_LIMIT = 1u << 22;   // try_wait iterations before giving up
 constexpr unsigned STAGED_DRAIN_LIMIT = 1u << 16;  // second, shorter wait after a timeout
@@ -95,7 +96,7 @@ __device__ __forceinline__ void staged_issue(const S* __restrict__ src, const KP
 }
 
 template <int DIM, class S, bool TRT>
-__global__ void __launch_bounds__(STAGED_THREADS) step_staged_kernel(const S* __restrict__ src, S* __restrict__ dst,
+__global__ void __launch_bounds__(STAGED_THREADS, STAGED_MIN_BLOCKS) step_staged_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                                      const KParams p, const StagedInfo si) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;

@@ -81,6 +81,24 @@ _SIGS = {
                                    C.POINTER(C.c_int)]),
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "tlbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                    C.POINTER(tlbm_params)]),
+    "tlbm_batch_required_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "tlbm_batch_bind_memory": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "tlbm_batch_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tlbm_batch_init": (C.c_int, [C.c_void_p, C.c_double]),
+    "tlbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "tlbm_batch_set_variant": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "tlbm_batch_get_variant": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
+    "tlbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
+    "tlbm_batch_instance": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "tlbm_batch_nusselt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "tlbm_batch_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "tlbm_batch_macros": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int]),
+    "tlbm_batch_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "tlbm_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "tlbm_batch_destroy": (None, [C.c_void_p]),
     "tlbm_last_error": (C.c_char_p, [C.c_void_p]),
     "tlbm_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "tlbm_destroy": (None, [C.c_void_p]),
@@ -367,3 +385,170 @@ class Sim:
     @property
     def launches(self):
         return tlbm_launch_count(self.h)
+
+
+# ------------------------------------------------------------------ batched ensemble
+
+def _bcheck(b, rc):
+    if rc != TLBM_OK:
+        msg = lib().tlbm_batch_last_error(b)
+        raise TlbmError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def tlbm_batch_create(instances, lattice, precision, params: tlbm_params | None = None):
+    """instances: sequence of (nx, ny, nz, Ra, Pr, Ma, seed)."""
+    arr = (tlbm_instance * len(instances))()
+    for k, (nx, ny, nz, Ra, Pr, Ma, seed) in enumerate(instances):
+        arr[k] = tlbm_instance(int(nx), int(ny), int(nz), float(Ra), float(Pr), float(Ma), int(seed))
+    b = C.c_void_p()
+    rc = lib().tlbm_batch_create(C.byref(b), len(instances), C.cast(arr, C.c_void_p), int(lattice), int(precision),
+                                 C.byref(params) if params is not None else None)
+    _bcheck(None, rc)
+    return b
+
+
+def tlbm_batch_required_bytes(b) -> int:
+    n = C.c_size_t()
+    _bcheck(b, lib().tlbm_batch_required_bytes(b, C.byref(n)))
+    return n.value
+
+
+def tlbm_batch_bind_memory(b, dev_ptr: int, nbytes: int):
+    _bcheck(b, lib().tlbm_batch_bind_memory(b, C.c_void_p(dev_ptr), nbytes))
+
+
+def tlbm_batch_set_stream(b, stream_handle: int):
+    _bcheck(b, lib().tlbm_batch_set_stream(b, C.c_void_p(stream_handle)))
+
+
+def tlbm_batch_init(b, noise_amp: float):
+    _bcheck(b, lib().tlbm_batch_init(b, float(noise_amp)))
+
+
+def tlbm_batch_step(b, n: int):
+    _bcheck(b, lib().tlbm_batch_step(b, C.c_int64(n)))
+
+
+def tlbm_batch_set_variant(b, vec=0, form=0, block_x=0, block_y=0, graph_steps=16):
+    _bcheck(b, lib().tlbm_batch_set_variant(b, int(vec), int(form), int(block_x), int(block_y), int(graph_steps)))
+
+
+def tlbm_batch_get_variant(b):
+    v = [C.c_int() for _ in range(5)]
+    _bcheck(b, lib().tlbm_batch_get_variant(b, *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def tlbm_batch_autotune(b, trials: int = 5):
+    _bcheck(b, lib().tlbm_batch_autotune(b, int(trials)))
+
+
+def tlbm_batch_instance(b, idx: int):
+    h = C.c_void_p()
+    _bcheck(b, lib().tlbm_batch_instance(b, int(idx), C.byref(h)))
+    return h
+
+
+def tlbm_batch_nusselt(b, n: int) -> list:
+    out = (C.c_double * n)()
+    _bcheck(b, lib().tlbm_batch_nusselt(b, out))
+    return list(out)
+
+
+def tlbm_batch_status(b, n: int) -> list:
+    out = (C.c_int * n)()
+    _bcheck(b, lib().tlbm_batch_status(b, out))
+    return [bool(v) for v in out]
+
+
+def tlbm_batch_macros(b, idx, rho=None, ux=None, uy=None, uz=None, T=None, out_dtype=TLBM_OUT_F64):
+    _bcheck(b, lib().tlbm_batch_macros(b, int(idx), _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T),
+                                       int(out_dtype)))
+
+
+def tlbm_batch_launch_count(b) -> int:
+    n = C.c_int64()
+    _bcheck(b, lib().tlbm_batch_launch_count(b, C.byref(n)))
+    return n.value
+
+
+def tlbm_batch_last_error(b) -> str:
+    m = lib().tlbm_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def tlbm_batch_destroy(b):
+    if b:
+        lib().tlbm_batch_destroy(b)
+
+
+class Batch:
+    """An ensemble of independent cells stepped together; device memory is a
+    torch uint8 tensor bound to the batch."""
+
+    def __init__(self, instances, lattice=TLBM_D2Q9_D2Q5, precision=TLBM_FP32, stream=None, **params):
+        import torch
+
+        self.instances = list(instances)
+        self.n = len(self.instances)
+        self.lattice = lattice
+        self.params = tlbm_default_params(**params)
+        self.b = tlbm_batch_create(self.instances, lattice, precision, self.params)
+        self.nbytes = tlbm_batch_required_bytes(self.b)
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        tlbm_batch_set_stream(self.b, s.cuda_stream)
+        tlbm_batch_bind_memory(self.b, self.mem.data_ptr(), self.nbytes)
+
+    def close(self):
+        if getattr(self, "b", None):
+            tlbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, noise_amp):
+        tlbm_batch_init(self.b, noise_amp)
+
+    def step(self, n=1):
+        tlbm_batch_step(self.b, n)
+
+    def set_variant(self, vec=0, form=0, block_x=0, block_y=0, graph_steps=16):
+        tlbm_batch_set_variant(self.b, vec, form, block_x, block_y, graph_steps)
+
+    @property
+    def variant(self):
+        return tlbm_batch_get_variant(self.b)
+
+    def autotune(self, trials=5):
+        tlbm_batch_autotune(self.b, trials)
+
+    def nusselt(self):
+        return tlbm_batch_nusselt(self.b, self.n)
+
+    def status(self):
+        return tlbm_batch_status(self.b, self.n)
+
+    def instance(self, idx):
+        return tlbm_batch_instance(self.b, idx)
+
+    def get_populations(self, idx):
+        import numpy as np
+
+        nx, ny, nz = self.instances[idx][:3]
+        shape = (nz, ny, nx) if self.lattice == TLBM_D3Q19_D3Q7 else (ny, nx)
+        qf, qg = (9, 5) if self.lattice == TLBM_D2Q9_D2Q5 else (19, 7)
+        f = np.zeros((qf,) + shape)
+        g = np.zeros((qg,) + shape)
+        tlbm_get_populations(self.instance(idx), f, g)
+        return f, g
+
+    @property
+    def launches(self):
+        return tlbm_batch_launch_count(self.b)

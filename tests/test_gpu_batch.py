@@ -1,0 +1,103 @@
+"""Batched ensemble: every instance of a batch evolves exactly as the same cell
+stepped on its own, for every batch variant and with CUDA-graph step blocks;
+small instances also match the FP64 oracle."""
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_03160_gb300 import tlbm
+
+    tlbm.lib()
+    return tlbm
+
+
+def _draws(n, sizes, seed=4, lattice=0):
+    out = []
+    for N, Ra, Pr, s in inputs.ensemble_draws(seed, n, sizes=sizes, log_ra=(5.0, 7.0)):
+        out.append((N, N + 3, N - 2 if lattice else 1, Ra, Pr, 0.1, s))
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_batch_equals_single_instances(T, prec):
+    inst = _draws(7, (33, 65, 129))
+    b = T.Batch(inst, lattice=0, precision=prec)
+    b.init(1e-3)
+    b.step(37)  # a graph block of 16 steps, twice, plus single launches
+    singles = []
+    for nx, ny, nz, Ra, Pr, Ma, seed in inst:
+        s = T.Sim(nx, ny, nz, lattice=0, Ra=Ra, Pr=Pr, Ma=Ma, precision=prec)
+        v, form, bx, by = b.variant[:4]
+        s.set_variant(v, form, bx, by)
+        s.init(seed, 1e-3)
+        s.step(37)
+        singles.append(s.get_populations())
+    for k in range(len(inst)):
+        fb, gb = b.get_populations(k)
+        fs, gs = singles[k]
+        # same arithmetic in another kernel: equal up to the compiler's
+        # multiply-add contraction choices (one rounding of the storage type)
+        tol = {0: 1e-13, 1: 1e-6, 2: 1e-3, 3: 4e-3}[prec]
+        assert np.abs(fb - fs).max() <= tol and np.abs(gb - gs).max() <= tol, k
+
+
+def test_batch_3d_and_oracle(T, O):
+    inst = [(9, 11, 7, 1e5, 0.71, 0.1, 3), (13, 9, 10, 3e5, 7.0, 0.1, 4), (17, 8, 9, 1e6, 0.71, 0.1, 5)]
+    b = T.Batch(inst, lattice=1, precision=0)
+    b.init(1e-3)
+    b.step(20)
+    for k, (nx, ny, nz, Ra, Pr, Ma, seed) in enumerate(inst):
+        o = O.Sim(nx, ny, nz, lattice=1, Ra=Ra, Pr=Pr, Ma=Ma)
+        o.init(seed, 1e-3)
+        o.step(20)
+        fb, gb = b.get_populations(k)
+        fo, go = o.get_populations()
+        assert np.abs(fb - fo).max() < 1e-12 and np.abs(gb - go).max() < 1e-12
+
+
+def test_batch_variants_and_autotune_keep_state(T):
+    inst = _draws(9, (129, 257))
+    b = T.Batch(inst, lattice=0, precision=1)
+    b.init(1e-3)
+    b.step(6)
+    before = [b.get_populations(k) for k in (0, 4, 8)]
+    b.autotune(3)
+    after = [b.get_populations(k) for k in (0, 4, 8)]
+    for (f0, g0), (f1, g1) in zip(before, after):
+        assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    ref = None
+    for vec, form, bx, by, gs in ((4, 2, 32, 1, 16), (2, 2, 64, 2, 0), (4, 1, 32, 4, 4), (0, 0, 0, 0, 2)):
+        c = T.Batch(inst, lattice=0, precision=1)
+        c.set_variant(vec, form, bx, by, gs)
+        c.init(1e-3)
+        c.step(11)
+        pops = [c.get_populations(k) for k in (0, 4, 8)]
+        if ref is None:
+            ref = pops
+        else:
+            for (f0, g0), (f1, g1) in zip(ref, pops):
+                assert np.abs(f0 - f1).max() < 2e-6 and np.abs(g0 - g1).max() < 2e-6
+        c.close()
+
+
+def test_batch_reductions_and_status(T):
+    inst = _draws(5, (65, 129))
+    b = T.Batch(inst, lattice=0, precision=1)
+    b.init(1e-3)
+    b.step(10)
+    nus = b.nusselt()
+    assert len(nus) == 5 and all(np.isfinite(nus))
+    assert b.status() == [False] * 5
+    for k in range(5):
+        assert abs(T.tlbm_nusselt(b.instance(k)) - nus[k]) == 0.0
+    assert b.launches >= 10
