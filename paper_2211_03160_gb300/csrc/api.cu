@@ -372,7 +372,7 @@ static VariantDefault default_variant(int dim, int prec) {
     }
     switch (prec) {
     case TLBM_FP64: return {1, 32, 4};
-    case TLBM_FP32: return {2, 32, 4};
+    case TLBM_FP32: return {1, 32, 2};
     default: return {1, 32, 4};
     }
 }
@@ -571,6 +571,9 @@ extern "C" int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes) {
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaPointerGetAttributes");
     if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
         return fail(h, TLBM_ERR_ARG, "dev_ptr is not device memory");
+    // the staged kernel's status word starts cleared
+    e = cudaMemset((char*)dev_ptr + h->status_off, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
     h->mem = (char*)dev_ptr;
     h->mem_bytes = bytes;
     h->buf[0] = h->mem;
@@ -770,6 +773,8 @@ extern "C" int tlbm_set_populations(tlbm_t h, const double* host_f, const double
     const Window full = {0, 0, 0, h->nx, h->ny, h->nz};
     double* stage = (double*)(h->mem + h->stage_off);
     cudaError_t e = cudaMemsetAsync(h->mem, 0, 2 * h->popset_bytes, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    e = cudaMemsetAsync(h->mem + h->status_off, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     h->cur = 0;
     for (int pop = 0; pop < h->qf + h->qg; ++pop) {

@@ -304,18 +304,29 @@ template <> struct Lat<3> { using F = D3Q19; using G = D3Q7; };
 // operator M^-1 S M of Eq. (5) equals sp on the symmetric part and sm on the
 // antisymmetric part of each pair (i, ibar), and M^-1 (I - S/2) M Ftilde
 // splits the same way (the conserved moments' rates cancel out, see the MRT
-// form above).  Likewise for the thermal operator of Eq. (7).  Deviation form:
-//   E_i = f_eq,i - w_i = w_i [drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2)],
-//   G_i = w_i [3 (e - u).F + 9 (e.u)(e.F)]  (Guo).
-template <int DIM, class C>
+// form above).  Likewise for the thermal operator of Eq. (7).  In deviation
+// form, with E_i = f_eq,i - w_i = w_i [drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2)]
+// and the Guo source G_i = w_i [3 (e - u).F + 9 (e.u)(e.F)], a pair updates as
+//   d_i+    = c1 d_i + c2 d_ibar + Ks + Ka,   d_ibar+ = c1 d_ibar + c2 d_i + Ks - Ka,
+//   c1 = 1 - (sp + sm)/2,  c2 = (sm - sp)/2,
+//   Ks = sp E_i^s + (1 - sp/2) G_i^s = w_i [K0 + e.u (4.5 sp rho e.u + 9 (1 - sp/2) e.F)],
+//   Ka = sm E_i^a + (1 - sm/2) G_i^a = w_i [3 sm rho e.u + 3 (1 - sm/2) e.F],
+//   K0 = sp drho - 1.5 sp rho u^2 - 3 (1 - sp/2) u.F   (one value per node),
+// and the rest population as d_0+ = (1 - sp) d_0 + w_0 K0.  The thermal pairs:
+//   g_i+ = t1 g_i + t2 g_ibar + qp wT T + (qm/2) e.u T  (and - for ibar),
+//   t1 = 1 - (qp + qm)/2, t2 = (qm - qp)/2, wT = omega/2;  g_0+ = (1 - qp) g_0 + qp (1 - (q-1) wT) T.
+// SCALED: the inputs and outputs are the stored values d_i * scale and
+// g_i * scale (offset storage); every term is linear in them except through the
+// node's rho, u and T, which are formed unscaled.
+template <int DIM, class C, bool SCALED>
 __device__ __forceinline__ void collide_trt(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q], const KParams& p) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
     using P = PV<C>;
-    C drho = C(0), jx = C(0), jy = C(0), jz = C(0), T = C(0);
+    C drs = C(0), jx = C(0), jy = C(0), jz = C(0), Ts = C(0);
     static_for<LF::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        drho += d[i];
+        drs += d[i];
         if constexpr (LF::e(i, 0) == 1) jx += d[i];
         if constexpr (LF::e(i, 0) == -1) jx -= d[i];
         if constexpr (LF::e(i, 1) == 1) jy += d[i];
@@ -323,75 +334,76 @@ __device__ __forceinline__ void collide_trt(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<D
         if constexpr (LF::e(i, 2) == 1) jz += d[i];
         if constexpr (LF::e(i, 2) == -1) jz -= d[i];
     });
-    static_for<LG::Q>([&](auto ii) { T += g[decltype(ii)::value]; });
+    static_for<LG::Q>([&](auto ii) { Ts += g[decltype(ii)::value]; });
+    C sc = C(1), inv = C(1);
+    if constexpr (SCALED) {
+        sc = ScaleOf<C>::s(p);
+        inv = ScaleOf<C>::inv(p);
+    }
+    const C drho = SCALED ? drs * inv : drs;
+    const C T = SCALED ? Ts * inv : Ts;
     const C rho = C(1) + drho;
     const C buoy = P::gbeta(p) * T;
     const C Fx = rho * P::body(p, 0);
     const C Fy = rho * (DIM == 2 ? buoy + P::body(p, 1) : P::body(p, 1));
     const C Fz = DIM == 3 ? rho * (buoy + P::body(p, 2)) : C(0);
     const C ir = recip(rho);
-    const C ux = (jx + C(0.5) * Fx) * ir;
-    const C uy = (jy + C(0.5) * Fy) * ir;
-    const C uz = DIM == 3 ? (jz + C(0.5) * Fz) * ir : C(0);
+    const C hx = C(0.5) * Fx, hy = C(0.5) * Fy, hz = C(0.5) * Fz;
+    const C ux = (SCALED ? fma(jx, inv, hx) : jx + hx) * ir;
+    const C uy = (SCALED ? fma(jy, inv, hy) : jy + hy) * ir;
+    const C uz = DIM == 3 ? (SCALED ? fma(jz, inv, hz) : jz + hz) * ir : C(0);
     const C sp = P::sp(p), sm = P::sm(p), shp = P::shp(p), shm = P::shm(p);
     const C uu15 = C(1.5) * (ux * ux + uy * uy + uz * uz);
     const C uF3 = C(3) * (ux * Fx + uy * Fy + uz * Fz);
-    // rest population
+    const C K0 = sp * (drho - rho * uu15) - shp * uF3;
+    const C R1 = C(4.5) * sp * rho, R2 = C(9) * shp;
+    const C R3 = C(3) * sm * rho, R4 = C(3) * shm;
+    const C c1 = C(1) - C(0.5) * (sp + sm), c2 = C(0.5) * (sm - sp);
     {
         constexpr C w0 = weight<LF, C>(0);
-        const C E0 = w0 * (drho - rho * uu15);
-        const C G0 = -w0 * uF3;
-        d[0] = d[0] - sp * (d[0] - E0) + shp * G0;
+        d[0] = (C(1) - sp) * d[0] + (w0 * sc) * K0;
     }
     static_for<LF::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         constexpr int o = LF::opp(i);
         if constexpr (i != 0 && i < o) {
             constexpr int ex = LF::e(i, 0), ey = LF::e(i, 1), ez = LF::e(i, 2);
-            constexpr C w = weight<LF, C>(i);
+            const C ws = weight<LF, C>(i) * sc;
             C eu = C(0), eF = C(0);
             if constexpr (ex != 0) { eu += C(ex) * ux; eF += C(ex) * Fx; }
             if constexpr (ey != 0) { eu += C(ey) * uy; eF += C(ey) * Fy; }
             if constexpr (ez != 0) { eu += C(ez) * uz; eF += C(ez) * Fz; }
-            const C Es = w * (drho + rho * (C(4.5) * eu * eu - uu15));
-            const C Ea = w * C(3) * rho * eu;
-            const C Gs = w * (C(9) * eu * eF - uF3);
-            const C Ga = w * C(3) * eF;
-            const C ds = C(0.5) * (d[i] + d[o]);
-            const C da = C(0.5) * (d[i] - d[o]);
-            const C A = shp * Gs - sp * (ds - Es);
-            const C B = shm * Ga - sm * (da - Ea);
-            d[i] = d[i] + A + B;
-            d[o] = d[o] + A - B;
+            const C Ks = ws * (K0 + eu * (R1 * eu + R2 * eF));
+            const C Ka = ws * (R3 * eu + R4 * eF);
+            const C di = d[i], dob = d[o];
+            d[i] = c1 * di + c2 * dob + (Ks + Ka);
+            d[o] = c1 * dob + c2 * di + (Ks - Ka);
         }
     });
-    // thermal: g_eq,i = wT T + (e.u) T / 2 on the moving links, wT = omega/2
+    // thermal
     const C qp = P::qp(p), qm = P::qm(p);
     const C wT = C(0.5) * P::omega(p);
-    const C geqs = wT * T;
-    {
-        const C g0eq = T - C(LG::Q - 1) * geqs;
-        g[0] = g[0] - qp * (g[0] - g0eq);
-    }
+    const C t1 = C(1) - C(0.5) * (qp + qm), t2 = C(0.5) * (qm - qp);
+    const C Ks_T = qp * wT * Ts;        // scaled like g
+    const C ka_T = C(0.5) * qm * Ts;    // times e.u
+    g[0] = (C(1) - qp) * g[0] + qp * (C(1) - C(LG::Q - 1) * wT) * Ts;
     static_for<LG::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         constexpr int o = LG::opp(i);
         if constexpr (i != 0 && i < o) {
             constexpr int ex = LG::e(i, 0), ey = LG::e(i, 1), ez = LG::e(i, 2);
             const C eu = ex != 0 ? C(ex) * ux : (ey != 0 ? C(ey) * uy : C(ez) * uz);
-            const C gs = C(0.5) * (g[i] + g[o]);
-            const C ga = C(0.5) * (g[i] - g[o]);
-            const C A = -qp * (gs - geqs);
-            const C B = -qm * (ga - C(0.5) * eu * T);
-            g[i] = g[i] + A + B;
-            g[o] = g[o] + A - B;
+            const C Ka = ka_T * eu;
+            const C gi = g[i], go = g[o];
+            g[i] = t1 * gi + t2 * go + (Ks_T + Ka);
+            g[o] = t1 * go + t2 * gi + (Ks_T - Ka);
         }
     });
 }
 
-template <int DIM, bool TRT, class C>
+template <int DIM, bool TRT, class C, bool SCALED = false>
 __device__ __forceinline__ void collide(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q], const KParams& p) {
-    if constexpr (TRT) collide_trt<DIM, C>(d, g, p);
+    if constexpr (TRT) collide_trt<DIM, C, SCALED>(d, g, p);
     else if constexpr (DIM == 2) collide_2d<C>(d, g, p);
     else collide_3d<C>(d, g, p);
 }
@@ -544,7 +556,29 @@ __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams&
 
 // ------------------------------------------------------------------ step kernel
 
-// decode a raw stored value (already converted to C) into the flow deviation
+// decode a raw stored value (already converted to C) into the flow deviation;
+// with KS (keep scaled) offset storage stays in its scaled domain
+template <class LF, class S, class C, bool KS>
+__device__ __forceinline__ C raw_to_dev_k(C raw, int i, C inv_scale) {
+    if constexpr (Storage<S>::offset) return KS ? raw : raw * inv_scale;
+    else return raw - weight<LF, C>(i);
+}
+template <class S, class C, bool KS>
+__device__ __forceinline__ C raw_to_g_k(C raw, C inv_scale) {
+    if constexpr (Storage<S>::offset) return KS ? raw : raw * inv_scale;
+    else return raw;
+}
+template <class LF, class S, class C, bool KS>
+__device__ __forceinline__ S enc_f_k(C d, int i, C scale) {
+    if constexpr (Storage<S>::offset) return from_c<S>(KS ? d : d * scale);
+    else return from_c<S>(weight<LF, C>(i) + d);
+}
+template <class S, class C, bool KS>
+__device__ __forceinline__ S enc_g_k(C g, C scale) {
+    if constexpr (Storage<S>::offset) return from_c<S>(KS ? g : g * scale);
+    else return from_c<S>(g);
+}
+
 template <class LF, class S, class C>
 __device__ __forceinline__ C raw_to_dev(C raw, int i, C inv_scale) {
     if constexpr (Storage<S>::offset) return raw * inv_scale;
@@ -558,7 +592,7 @@ __device__ __forceinline__ C raw_to_g(C raw, C inv_scale) {
 
 // Pull the pre-collision populations of nodes x0 .. x0+VEC-1 whose own slot in
 // plane 0 is `own`: f as deviations d_i = f_i - w_i, g as values.
-template <int DIM, class S, int VEC, class C>
+template <int DIM, class S, int VEC, class C, bool KS>
 __device__ __forceinline__ void pull_node_vec(const S* __restrict__ own, const KParams& p, int lane,
                                               C (&f)[Lat<DIM>::F::Q][VEC], C (&g)[Lat<DIM>::G::Q][VEC]) {
     using LF = typename Lat<DIM>::F;
@@ -569,14 +603,14 @@ __device__ __forceinline__ void pull_node_vec(const S* __restrict__ own, const K
         C t[VEC];
         pull_row<S, VEC, LF::e(i, 0), C>(own + p.loff[i], lane, t);
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) f[i][k] = raw_to_dev<LF, S, C>(t[k], i, inv_scale);
+        for (int k = 0; k < VEC; ++k) f[i][k] = raw_to_dev_k<LF, S, C, KS>(t[k], i, inv_scale);
     });
     static_for<LG::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         C t[VEC];
         pull_row<S, VEC, LG::e(i, 0), C>(own + p.loff[LF::Q + i], lane, t);
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g<S, C>(t[k], inv_scale);
+        for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g_k<S, C, KS>(t[k], inv_scale);
     });
 }
 
@@ -625,9 +659,10 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
     const int x0ld = min(x0, p.xmax_load);
     const C scale = ScaleOf<C>::s(p);
     const long long row = L.row(y, z);
+    constexpr bool KS = TRT && Storage<S>::offset;  // TRT works on the stored, scaled values
 
     C f[QF][VEC], g[QG][VEC];
-    pull_node_vec<DIM, S, VEC, C>(src + row + x0ld, p, lane, f, g);
+    pull_node_vec<DIM, S, VEC, C, KS>(src + row + x0ld, p, lane, f, g);
 
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
@@ -636,7 +671,7 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
         for (int i = 0; i < QF; ++i) fd[i] = f[i][k];
 #pragma unroll
         for (int i = 0; i < QG; ++i) gd[i] = g[i][k];
-        collide<DIM, TRT, C>(fd, gd, p);
+        collide<DIM, TRT, C, KS>(fd, gd, p);
 #pragma unroll
         for (int i = 0; i < QF; ++i) f[i][k] = fd[i];
 #pragma unroll
@@ -650,14 +685,14 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
             constexpr int i = decltype(ii)::value;
             S v[VEC];
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = enc_f<LF, S, C>(f[i][k], i, scale);
+            for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
             st_vec<S, VEC>(own + p.soff[i], v);
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = enc_g<S, C>(g[i][k], scale);
+            for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
             st_vec<S, VEC>(own + p.soff[QF + i], v);
         });
     } else {
@@ -666,11 +701,11 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
             if (x0 + k < L.nx) {
                 static_for<QF>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    own[p.soff[i] + k] = enc_f<LF, S, C>(f[i][k], i, scale);
+                    own[p.soff[i] + k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
                 });
                 static_for<QG>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    own[p.soff[QF + i] + k] = enc_g<S, C>(g[i][k], scale);
+                    own[p.soff[QF + i] + k] = enc_g_k<S, C, KS>(g[i][k], scale);
                 });
             }
         }
@@ -681,12 +716,13 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
                       (DIM == 3 && (z == 0 || z == L.nz - 1));
     if (edge) {
         C post[(QF + QG) * VEC];
+        const C un = KS ? ScaleOf<C>::inv(p) : C(1);  // the wall rules take unscaled values
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
 #pragma unroll
-            for (int i = 0; i < QF; ++i) post[i * VEC + k] = f[i][k];
+            for (int i = 0; i < QF; ++i) post[i * VEC + k] = KS ? f[i][k] * un : f[i][k];
 #pragma unroll
-            for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = g[i][k];
+            for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = KS ? g[i][k] * un : g[i][k];
         }
         edge_writes<DIM, S, VEC, C>(dst, p, x0, y, z, post);
     }
