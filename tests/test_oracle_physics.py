@@ -318,3 +318,40 @@ def test_convection_onset_near_1708(O):
     p = np.polyfit(ras, rates, 1)
     ra_c = -p[1] / p[0]
     assert abs(ra_c / 1707.76 - 1) < 0.02, ra_c
+
+
+# ------------------------------------------------------------------ coupling and diagnostics
+
+@pytest.mark.parametrize("lattice,shape", [(D2, (9, 12, 1)), (D3, (7, 6, 9))])
+def test_buoyancy_enters_the_velocity_along_gravity(O, lattice, shape):
+    """Fluid at rest (sum e f = 0): u = F/(2 rho) with F = rho g beta T along +y
+    in 2D and +z in 3D (§2.2), so u = g beta T / 2 on that axis, 0 elsewhere."""
+    nx, ny, nz = shape
+    s = O.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1)
+    s.init(4, 1e-2)
+    d = s.derived()
+    m = s.macros()
+    up, others = ("uy", ("ux", "uz")) if lattice == D2 else ("uz", ("ux", "uy"))
+    assert np.abs(m[up] - 0.5 * d["gbeta"] * m["T"]).max() < 1e-18
+    for k in others:
+        assert np.abs(m[k]).max() == 0.0
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_nusselt_of_a_uniform_flow(O, walls):
+    """Nu = 1 + L <u_h T> / (alpha dT) evaluated on a uniform state: u_h = U0
+    and T = T0 everywhere give Nu = 1 + L U0 T0 / alpha (the definition used for
+    the Nusselt number, L the extent along the heat-flux axis)."""
+    nx, ny = 12, 9
+    s = O.Sim(nx, ny, Ra=1e5, Pr=0.71, Ma=0.1, walls=walls, gbeta=0.0)
+    d = s.derived()
+    U0, T0 = 0.02, 0.3
+    u = [U0, 0.0, 0.0] if walls == 1 else [0.0, U0, 0.0]
+    e, w, _, M, Mi = O.velocity_set(0)
+    feq = Mi @ O.flow_meq(0, 1.0, u)
+    geq = O.thermal_geq(0, d["a_T"], T0, u)
+    f = np.broadcast_to(feq[:, None, None], (9, ny, nx)).copy()
+    g = np.broadcast_to(geq[:, None, None], (5, ny, nx)).copy()
+    s.set_populations(f, g)
+    L = nx if walls == 1 else ny
+    assert abs(s.nusselt() - (1.0 + L * U0 * T0 / d["alpha"])) < 1e-12
