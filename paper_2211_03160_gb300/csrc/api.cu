@@ -367,7 +367,7 @@ static VariantDefault default_variant(int dim, int prec) {
         switch (prec) {
         case TLBM_FP64: return {2, 64, 1};
         case TLBM_FP32: return {4, 32, 1};
-        default: return {4, 32, 2};
+        default: return {4, 32, 4};
         }
     }
     switch (prec) {
