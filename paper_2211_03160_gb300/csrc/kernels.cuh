@@ -488,6 +488,12 @@ __device__ __forceinline__ void st_vec(S* __restrict__ p, const S (&v)[VEC]) {
 // lanes must call this together.
 template <class S, int VEC, int EX, class C>
 __device__ __forceinline__ void pull_row(const S* __restrict__ q, int lane, C (&out)[VEC]) {
+    if constexpr (VEC == 1) {
+        // one node per thread: a scalar load needs no alignment, fetch the
+        // shifted element directly
+        out[0] = to_c<C>(q[-EX]);
+        return;
+    }
     S v[VEC];
     ld_vec<S, VEC>(q, v);
     if constexpr (EX == 0) {
