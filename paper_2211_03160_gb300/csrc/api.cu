@@ -501,8 +501,8 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
                 ey = j < qf ? D3Q19::e(j, 1) : D3Q7::e(j - qf, 1);
                 ez = j < qf ? D3Q19::e(j, 2) : D3Q7::e(j - qf, 2);
             }
-            kp.soff[j] = (long long)j * kp.L.plane;
-            kp.loff[j] = kp.soff[j] - ey * P - ez * RP;
+            kp.soff[j] = (int)((long long)j * kp.L.plane);
+            kp.loff[j] = (int)((long long)j * kp.L.plane - ey * P - ez * RP);
         }
     }
     h->vec = default_variant(dim, precision).vec;
@@ -538,6 +538,10 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
     kp.scale = (float)scale;
     kp.inv_scale = (float)(1.0 / scale);
 
+    if ((long long)(h->qf + h->qg) * kp.L.plane + kp.L.P >= (1ll << 31)) {
+        delete h;
+        return fail(nullptr, TLBM_ERR_ARG, "cell too large: a population set must hold fewer than 2^31 elements");
+    }
     h->elem = precision == TLBM_FP64 ? 8 : (precision == TLBM_FP32 ? 4 : 2);
     h->popset_bytes = align_up((size_t)(h->qf + h->qg) * (size_t)kp.L.plane * h->elem, 256);
     h->red_off = 2 * h->popset_bytes;

@@ -71,8 +71,9 @@ struct KParams {
     // element offsets, relative to a node's own slot in plane 0, of the slot
     // each population j (flow planes first, then thermal) is pulled from, and
     // of the plane it is stored to
-    long long loff[2 * MAXQ];
-    long long soff[2 * MAXQ];
+    // (32-bit: a population set holds fewer than 2^31 elements)
+    int loff[2 * MAXQ];
+    int soff[2 * MAXQ];
 };
 
 // ------------------------------------------------------------------ storage
