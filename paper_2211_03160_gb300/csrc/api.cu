@@ -373,7 +373,7 @@ static VariantDefault default_variant(int dim, int prec) {
     switch (prec) {
     case TLBM_FP64: return {1, 32, 4};
     case TLBM_FP32: return {1, 32, 2};
-    default: return {1, 32, 4};
+    default: return {1, 32, 8};
     }
 }
 static int default_vec(int dim, int prec) { return default_variant(dim, prec).vec; }
