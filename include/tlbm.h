@@ -143,6 +143,11 @@ TLBM_API int tlbm_set_stream(tlbm_t h, void* cuda_stream);
  * r = (splitmix64(seed ^ splitmix64(n)) >> 11) * 2^-53 for node n. */
 TLBM_API int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp);
 
+/* Initial state (t = 0) from given device FP32 fields of nx*ny*nz values (x
+ * fastest): f = f_eq(rho = 1, u), g = g_eq(T, u) (a warm start).  T is
+ * required; a NULL velocity component is 0.  Asynchronous. */
+TLBM_API int tlbm_init_fields(tlbm_t h, const float* T, const float* ux, const float* uy, const float* uz);
+
 /* Advance n >= 0 time steps (Eqs. (10)-(11), fused).  Asynchronous. */
 TLBM_API int tlbm_step(tlbm_t h, int64_t n);
 
@@ -245,6 +250,53 @@ TLBM_API int tlbm_batch_macros(tlbm_batch_t b, int idx, void* rho, void* ux, voi
 TLBM_API int tlbm_batch_launch_count(tlbm_batch_t b, int64_t* count);
 TLBM_API const char* tlbm_batch_last_error(tlbm_batch_t b);
 TLBM_API void tlbm_batch_destroy(tlbm_batch_t b);
+
+/* ---------------------------------------------------------------- learned warm start
+ * Layers of a small convolutional surrogate that predicts a statistically
+ * steady T/u/v field from (Ra, Pr) to start the solver from (no counterpart in
+ * the paper).  3x3 convolutions, stride 1, zero padding 1, NCHW, at most 32
+ * channels; BF16 operands on the tensor cores, FP32 accumulation.  All pointers
+ * are device pointers owned by the caller; every call is asynchronous on
+ * `stream` (a cudaStream_t, NULL = legacy stream) and returns TLBM_ERR_ARG for
+ * bad shapes or NULL pointers. */
+
+/* FP32 weights w[cout][cin][3][3] -> BF16 GEMM operand a[cout][Kp],
+ * Kp = 16 * ceil(9 cin / 16), zero-padded. */
+TLBM_API int tlbm_conv3x3_pack_weights(const float* w, int cout, int cin, void* a, void* stream);
+/* y[B][cout][H][W] (FP32) = bias + conv(x, w); x BF16 [B][cin][H][W]; a from
+ * tlbm_conv3x3_pack_weights; bias FP32 [cout] or NULL; y_act (BF16, optional)
+ * = relu(y) when relu != 0, else y. */
+TLBM_API int tlbm_conv3x3_forward(const void* x, const void* a, const float* bias, float* y, void* y_act, int B,
+                                  int cin, int cout, int H, int W, int relu, void* stream);
+/* dx[B][cin][H][W] (FP32) = gradient w.r.t. the input of the convolution with
+ * BF16 weights w_bf16[cout][cin][3][3], given dy (BF16 [B][cout][H][W]);
+ * at_workspace: BF16 scratch of 32 * 288 elements. */
+TLBM_API int tlbm_conv3x3_backward_data(const void* dy, const void* w_bf16, float* dx, int B, int cin, int cout,
+                                        int H, int W, void* at_workspace, void* stream);
+/* Bytes of workspace tlbm_conv3x3_backward_weight needs for this shape. */
+TLBM_API int tlbm_conv3x3_workspace_bytes(int B, int cin, int cout, int H, int W, size_t* bytes);
+/* dw[cout][cin][3][3] (FP32) = sum over pixels of dy * patches(x), summed in a
+ * fixed order; db[cout] = sum of dy (FP32 dy, optional).  x, dy_bf16: BF16. */
+TLBM_API int tlbm_conv3x3_backward_weight(const void* x, const void* dy_bf16, const float* dy, float* dw, float* db,
+                                          int B, int cin, int cout, int H, int W, void* workspace,
+                                          size_t workspace_bytes, void* stream);
+/* g = dx where y > 0 else 0, as FP32 and BF16 (n elements). */
+TLBM_API int tlbm_relu_backward(const float* dx, const float* y, long long n, float* g, void* g_bf16, void* stream);
+/* BF16 copy of an FP32 array. */
+TLBM_API int tlbm_to_bf16(const float* a, long long n, void* b, void* stream);
+/* Mean squared error of y against target (n elements): *loss_dev (FP64) and
+ * its gradient 2 (y - target) / n as FP32 and BF16; partial_dev holds 1024
+ * FP64 block sums (deterministic order). */
+TLBM_API int tlbm_mse_loss(const float* y, const float* target, long long n, float* g, void* g_bf16,
+                           double* loss_dev, double* partial_dev, void* stream);
+/* One Adam step (Kingma & Ba 2015) on FP32 weights w with moments m, v; t >= 1. */
+TLBM_API int tlbm_adam_step(float* w, const float* g, float* m, float* v, long long n, float lr, float b1,
+                            float b2, float eps, int t, void* stream);
+/* Vertex-aligned bilinear upsampling of `channels` planes of h x w to
+ * ((h-1) factor + 1) x ((w-1) factor + 1); coarse node (i, j) lands on fine node
+ * (factor i, factor j). */
+TLBM_API int tlbm_upsample_bilinear(const float* in, int channels, int h, int w, int factor, float* out,
+                                    void* stream);
 
 /* FP64 diagnostic sums of a population state without any device memory from
  * the caller beyond the state itself (the paper has no counterpart; this is a

@@ -30,6 +30,7 @@ UNITS = {
     "noalloc.cu": [],
     "step_staged.cu": [],
     "batch.cu": [],
+    "conv.cu": [],
 }
 
 

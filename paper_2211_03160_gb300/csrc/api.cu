@@ -128,6 +128,51 @@ __global__ void init_kernel(S* __restrict__ buf, const KParams p, uint64_t seed,
     }
 }
 
+// Initial state from given fields (warm start): f = f_eq(rho = 1, u) and
+// g = g_eq(T, u) at every node, written into the slots they are pulled from.
+template <int DIM, class S>
+__global__ void init_fields_kernel(S* __restrict__ buf, const KParams p, const float* __restrict__ Tf,
+                                   const float* __restrict__ uxf, const float* __restrict__ uyf,
+                                   const float* __restrict__ uzf) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    using C = typename Storage<S>::C;
+    const Layout& L = p.L;
+    const long long N = (long long)L.nx * L.ny * L.nz;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        node_xyz(n, L, x, y, z);
+        const double T = Tf[n];
+        const double u[3] = {uxf ? (double)uxf[n] : 0.0, uyf ? (double)uyf[n] : 0.0,
+                             (DIM == 3 && uzf) ? (double)uzf[n] : 0.0};
+        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        double nm[LG::Q];
+        for (int k = 0; k < LG::Q; ++k) nm[k] = 0.0;
+        nm[0] = T;
+        nm[1] = u[0] * T;
+        nm[2] = u[1] * T;
+        if (DIM == 3) nm[3] = u[2] * T;
+        nm[DIM == 2 ? 3 : 4] = p.a_T * T;
+        double gq[LG::Q];
+        populations<LG, double>(nm, gq);
+        const C scale = (C)p.scale;
+        static_for<LF::Q>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            const double eu = LF::e(i, 0) * u[0] + LF::e(i, 1) * u[1] + LF::e(i, 2) * u[2];
+            const double dev = (LF::w36(i) / 36.0) * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+            buf[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))] =
+                enc_f<LF, S, C>((C)dev, i, scale);
+        });
+        S* gb = buf + (long long)LF::Q * L.plane;
+        static_for<LG::Q>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            gb[(long long)i * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))] =
+                enc_g<S, C>((C)gq[i], scale);
+        });
+    }
+}
+
 // Host FP64 populations (one plane, nodes [n0, n0 + cnt)) -> pull slots.
 template <int DIM, class S>
 __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ stage, int pop, long long n0,
@@ -289,6 +334,11 @@ template <int DIM, class S>
 struct DiagKernels {
     static cudaError_t init(void* buf, const KParams& p, uint64_t seed, double amp, cudaStream_t s) {
         init_kernel<DIM, S><<<2048, 256, 0, s>>>((S*)buf, p, seed, amp);
+        return cudaGetLastError();
+    }
+    static cudaError_t init_fields(void* buf, const KParams& p, const float* T, const float* ux, const float* uy,
+                                   const float* uz, cudaStream_t s) {
+        init_fields_kernel<DIM, S><<<2048, 256, 0, s>>>((S*)buf, p, T, ux, uy, uz);
         return cudaGetLastError();
     }
     static cudaError_t scatter(void* buf, const double* st, int pop, long long n0, long long cnt, const Window& w,
@@ -603,6 +653,23 @@ extern "C" int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp) {
     h->cur = 0;
     e = with_types(h->dim, h->prec, [&](auto K) { return decltype(K)::init(h->buf[0], h->kp, seed, noise_amp, h->stream); });
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+    h->launches += 1;
+    h->t = 0;
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_init_fields(tlbm_t h, const float* T, const float* ux, const float* uy, const float* uz) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (!T) return fail(h, TLBM_ERR_ARG, "T is required");
+    cudaError_t e = cudaMemsetAsync(h->mem, 0, 2 * h->popset_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mem + h->status_off, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    h->cur = 0;
+    e = with_types(h->dim, h->prec, [&](auto K) {
+        return decltype(K)::init_fields(h->buf[0], h->kp, T, ux, uy, uz, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "init_fields kernel");
     h->launches += 1;
     h->t = 0;
     return TLBM_OK;

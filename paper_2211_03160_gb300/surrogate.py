@@ -1,0 +1,333 @@
+"""Learned warm start for the 2D Rayleigh-Benard cell.
+
+A 4-layer 3x3 convolutional network (32 channels, ReLU, BF16 weights on the
+tensor cores with FP32 accumulation and FP32 Adam master weights) maps, at the
+65 x 65 coarse nodes of a 513 x 513 cell, the input channels
+
+    conductive temperature, x, y (unit square), (log10 Ra - 7) / 1.5, (Pr - 3.855) / 3.145
+
+to the time-averaged temperature and velocity (T, u/U, v/U) of the statistically
+steady flow.  The prediction is upsampled vertex-aligned (coarse node (i, j) =
+fine node (8i, 8j)) and the solver starts from f = f_eq(1, u), g = g_eq(T, u)
+(tlbm_init_fields) instead of the conductive state.
+
+Training data are time averages of the batched solver's own runs.  The solver,
+the convolutions and their gradients, the loss, the optimiser, the upsampling
+and the initial state run in this project's CUDA kernels through the C ABI;
+torch holds the tensors and does the light bookkeeping (slicing and averaging
+snapshots, scaling the predicted velocity to lattice units).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+from . import tlbm
+
+COARSE = 65
+FINE = 513
+FACTOR = 8
+CIN, WIDTH, COUT, LAYERS = 5, 32, 3, 4
+
+
+# ------------------------------------------------------------------ features
+
+
+def features(Ra: float, Pr: float, n: int = COARSE, fine: int = FINE) -> np.ndarray:
+    """Input channels at the coarse nodes (vertex-aligned with the fine cell)."""
+    f = (fine - 1) // (n - 1)
+    idx = np.arange(n) * f  # fine node index of each coarse node
+    yy, xx = np.meshgrid(idx, idx, indexing="ij")
+    t_cond = 0.5 - (yy + 0.5) / fine
+    x = np.zeros((CIN, n, n), dtype=np.float32)
+    x[0] = t_cond
+    x[1] = xx / (fine - 1)
+    x[2] = yy / (fine - 1)
+    x[3] = (math.log10(Ra) - 7.0) / 1.5
+    x[4] = (Pr - 3.855) / 3.145
+    return x
+
+
+def draws(n: int, seed: int, log_ra=(6.0, 8.0), prs=(0.71, 7.0)):
+    r = np.random.default_rng(seed)
+    return [(float(10.0 ** r.uniform(*log_ra)), float(r.choice(prs)), 5000 + seed * 1000 + i) for i in range(n)]
+
+
+# ------------------------------------------------------------------ network
+
+
+class ConvNet:
+    """3x3 conv stack on the project's kernels; activations NCHW."""
+
+    def __init__(self, seed: int = 0, device: str = "cuda"):
+        import torch
+
+        self.torch = torch
+        rng = np.random.default_rng(seed)
+        chans = [CIN] + [WIDTH] * (LAYERS - 1) + [COUT]
+        self.shapes = list(zip(chans[1:], chans[:-1]))  # (cout, cin)
+        self.w, self.b, self.a, self.mw, self.vw, self.mb, self.vb = [], [], [], [], [], [], []
+        for cout, cin in self.shapes:
+            std = math.sqrt(2.0 / (9 * cin))
+            w = torch.tensor(rng.normal(0, std, (cout, cin, 3, 3)), dtype=torch.float32, device=device)
+            if cout == COUT:
+                w *= 0.1
+            self.w.append(w)
+            self.b.append(torch.zeros(cout, dtype=torch.float32, device=device))
+            kp = (cin * 9 + 15) // 16 * 16
+            self.a.append(torch.empty((cout, kp), dtype=torch.bfloat16, device=device))
+            self.mw.append(torch.zeros_like(w))
+            self.vw.append(torch.zeros_like(w))
+            self.mb.append(torch.zeros(cout, dtype=torch.float32, device=device))
+            self.vb.append(torch.zeros(cout, dtype=torch.float32, device=device))
+        self.t = 0
+        self.pack()
+
+    def pack(self):
+        for (cout, cin), w, a in zip(self.shapes, self.w, self.a):
+            tlbm.tlbm_conv3x3_pack_weights(w, cout, cin, a, self.torch.cuda.current_stream())
+
+    def forward(self, x16, B: int, H: int, W: int):
+        """x16: BF16 [B][CIN][H][W].  Returns the FP32 output and keeps what the
+        backward pass needs."""
+        torch = self.torch
+        s = torch.cuda.current_stream()
+        self.cache = []
+        a_in = x16
+        for k, (cout, cin) in enumerate(self.shapes):
+            y = torch.empty((B, cout, H, W), dtype=torch.float32, device=x16.device)
+            last = k == len(self.shapes) - 1
+            act = None if last else torch.empty((B, cout, H, W), dtype=torch.bfloat16, device=x16.device)
+            tlbm.tlbm_conv3x3_forward(a_in, self.a[k], self.b[k], y, act, B, cin, cout, H, W, 0 if last else 1, s)
+            self.cache.append((a_in, y))
+            a_in = act
+        return y
+
+    def backward(self, g32, g16, B: int, H: int, W: int):
+        torch = self.torch
+        s = torch.cuda.current_stream()
+        at = torch.empty(32 * 288, dtype=torch.bfloat16, device=g32.device)
+        self.gw = [None] * len(self.shapes)
+        self.gb = [None] * len(self.shapes)
+        for k in range(len(self.shapes) - 1, -1, -1):
+            cout, cin = self.shapes[k]
+            x_in, _ = self.cache[k]
+            ws = torch.empty(tlbm.tlbm_conv3x3_workspace_bytes(B, cin, cout, H, W), dtype=torch.uint8,
+                             device=g32.device)
+            dw = torch.empty((cout, cin, 3, 3), dtype=torch.float32, device=g32.device)
+            db = torch.empty(cout, dtype=torch.float32, device=g32.device)
+            tlbm.tlbm_conv3x3_backward_weight(x_in, g16, g32, dw, db, B, cin, cout, H, W, ws, s)
+            self.gw[k], self.gb[k] = dw, db
+            if k > 0:
+                wb = self.a_plain_bf16(k)
+                dx = torch.empty((B, cin, H, W), dtype=torch.float32, device=g32.device)
+                tlbm.tlbm_conv3x3_backward_data(g16, wb, dx, B, cin, cout, H, W, at, s)
+                _, y_prev = self.cache[k - 1]
+                g32 = torch.empty_like(dx)
+                g16 = torch.empty(dx.shape, dtype=torch.bfloat16, device=g32.device)
+                tlbm.tlbm_relu_backward(dx, y_prev, dx.numel(), g32, g16, s)
+
+    def a_plain_bf16(self, k):
+        """BF16 copy of layer k's weights in [cout][cin][3][3] order."""
+        torch = self.torch
+        w16 = torch.empty(self.w[k].shape, dtype=torch.bfloat16, device=self.w[k].device)
+        tlbm.tlbm_to_bf16(self.w[k], self.w[k].numel(), w16, torch.cuda.current_stream())
+        return w16
+
+    def adam(self, lr: float):
+        s = self.torch.cuda.current_stream()
+        self.t += 1
+        for k in range(len(self.shapes)):
+            tlbm.tlbm_adam_step(self.w[k], self.gw[k], self.mw[k], self.vw[k], self.w[k].numel(), lr, 0.9, 0.999,
+                                1e-8, self.t, s)
+            tlbm.tlbm_adam_step(self.b[k], self.gb[k], self.mb[k], self.vb[k], self.b[k].numel(), lr, 0.9, 0.999,
+                                1e-8, self.t, s)
+        self.pack()
+
+    def state(self):
+        return {"w": [w.cpu().numpy() for w in self.w], "b": [b.cpu().numpy() for b in self.b]}
+
+
+def train(net: ConvNet, X: np.ndarray, Y: np.ndarray, iters: int = 2000, lr: float = 2e-3, log_every: int = 200):
+    """Full-batch Adam on the mean squared error; returns the loss history."""
+    import torch
+
+    B, _, H, W = X.shape
+    s = torch.cuda.current_stream()
+    x32 = torch.tensor(X, dtype=torch.float32, device="cuda")
+    x16 = torch.empty(x32.shape, dtype=torch.bfloat16, device="cuda")
+    tlbm.tlbm_to_bf16(x32, x32.numel(), x16, s)
+    tgt = torch.tensor(Y, dtype=torch.float32, device="cuda")
+    g32 = torch.empty_like(tgt)
+    g16 = torch.empty(tgt.shape, dtype=torch.bfloat16, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    part = torch.zeros(1024, dtype=torch.float64, device="cuda")
+    hist = []
+    for it in range(1, iters + 1):
+        y = net.forward(x16, B, H, W)
+        tlbm.tlbm_mse_loss(y, tgt, y.numel(), g32, g16, loss, part, s)
+        net.backward(g32, g16, B, H, W)
+        net.adam(lr if it < 0.7 * iters else lr * 0.2)
+        if it == 1 or it % log_every == 0 or it == iters:
+            hist.append((it, float(loss.item())))
+    return hist
+
+
+def predict(net: ConvNet, Ra: float, Pr: float):
+    """Coarse (3, 65, 65) FP32 prediction on the device: T, u/U, v/U."""
+    import torch
+
+    s = torch.cuda.current_stream()
+    x32 = torch.tensor(features(Ra, Pr)[None], dtype=torch.float32, device="cuda")
+    x16 = torch.empty(x32.shape, dtype=torch.bfloat16, device="cuda")
+    tlbm.tlbm_to_bf16(x32, x32.numel(), x16, s)
+    return net.forward(x16, 1, COARSE, COARSE)[0]
+
+
+def warm_start(h, coarse, U: float):
+    """Upsample a coarse (T, u/U, v/U) prediction to the fine cell and start the
+    solver from it."""
+    import torch
+
+    s = torch.cuda.current_stream()
+    fine = torch.empty((3, FINE, FINE), dtype=torch.float32, device="cuda")
+    tlbm.tlbm_upsample_bilinear(coarse.contiguous(), 3, COARSE, COARSE, FACTOR, fine, s)
+    T = fine[0].clamp(-0.5, 0.5).contiguous()
+    ux = (fine[1] * U).contiguous()
+    uy = (fine[2] * U).contiguous()
+    tlbm.tlbm_init_fields(h, T, ux, uy, None)
+
+
+# ------------------------------------------------------------------ data and evaluation
+
+
+def free_fall_steps(n: int = FINE, Ma: float = 0.1) -> int:
+    return int(math.ceil(n / (Ma / math.sqrt(3.0))))
+
+
+def generate(draw_list, warm_tf: float, avg_tf: float, samples: int, precision=tlbm.TLBM_FP32):
+    """Time-averaged coarse (T, u/U, v/U) of each draw's statistically steady run."""
+    import torch
+
+    tf = free_fall_steps()
+    U = 0.1 / math.sqrt(3.0)
+    inst = [(FINE, FINE, 1, Ra, Pr, 0.1, seed) for Ra, Pr, seed in draw_list]
+    b = tlbm.Batch(inst, lattice=tlbm.TLBM_D2Q9_D2Q5, precision=precision)
+    b.init(1e-3)
+    b.step(int(warm_tf * tf))
+    every = max(1, int(avg_tf * tf / samples))
+    acc = torch.zeros((len(inst), 3, COARSE, COARSE), dtype=torch.float64, device="cuda")
+    T = torch.empty((FINE, FINE), dtype=torch.float32, device="cuda")
+    ux = torch.empty_like(T)
+    uy = torch.empty_like(T)
+    for _ in range(samples):
+        b.step(every)
+        for k in range(len(inst)):
+            tlbm.tlbm_batch_macros(b.b, k, None, ux, uy, None, T, tlbm.TLBM_OUT_F32)
+            acc[k, 0] += T[::FACTOR, ::FACTOR]
+            acc[k, 1] += ux[::FACTOR, ::FACTOR] / U
+            acc[k, 2] += uy[::FACTOR, ::FACTOR] / U
+    status = b.status()
+    b.close()
+    return (acc / samples).float().cpu().numpy(), status
+
+
+def steps_to_steady(nu: np.ndarray, dt: int, window: int, ref: float, tol: float = 0.01, hold: int = 2):
+    """First step after which the trailing mean of Nu over `window` samples
+    stays within tol of ref for hold * window samples (None if never)."""
+    n = len(nu)
+    if n < window:
+        return None
+    tm = np.convolve(nu, np.ones(window) / window, mode="valid")  # tm[k] = mean(nu[k : k+window])
+    ok = np.abs(tm - ref) <= tol * abs(ref)
+    need = hold * window
+    for k in range(len(ok)):
+        if ok[k:k + need].all() and len(ok[k:k + need]) == need:
+            return (k + window) * dt
+    return None
+
+
+def evaluate(net: ConvNet, draw_list, run_tf: float, ref_tf: float, samples_per_tf: int = 16,
+             precision=tlbm.TLBM_FP32):
+    """Conductive start vs learned warm start on the same draws (one batch)."""
+    import torch
+
+    tf = free_fall_steps()
+    U = 0.1 / math.sqrt(3.0)
+    n = len(draw_list)
+    inst = [(FINE, FINE, 1, Ra, Pr, 0.1, seed) for Ra, Pr, seed in draw_list] * 2
+    b = tlbm.Batch(inst, lattice=tlbm.TLBM_D2Q9_D2Q5, precision=precision)
+    b.init(1e-3)
+    for k, (Ra, Pr, _) in enumerate(draw_list):
+        warm_start(b.instance(n + k), predict(net, Ra, Pr), U)
+    torch.cuda.synchronize()
+    dt = max(1, tf // samples_per_tf)
+    total = int(run_tf * samples_per_tf)
+    nus = np.zeros((2 * n, total))
+    for s_ in range(total):
+        b.step(dt)
+        nus[:, s_] = b.nusselt()
+    status = b.status()
+    b.close()
+    window = samples_per_tf // 2  # half a free-fall time
+    out = []
+    ref_samples = int(ref_tf * samples_per_tf)
+    for k, (Ra, Pr, seed) in enumerate(draw_list):
+        ref = float(nus[k, -ref_samples:].mean())
+        cold = steps_to_steady(nus[k], dt, window, ref)
+        warm = steps_to_steady(nus[n + k], dt, window, ref)
+        out.append({"Ra": Ra, "Pr": Pr, "Nu_ref": ref, "steps_conductive": cold, "steps_warm": warm,
+                    "diverged": bool(status[k] or status[n + k])})
+    return out
+
+
+def main(argv=None):
+    import torch
+
+    ap = argparse.ArgumentParser(description="train and evaluate the learned warm start")
+    ap.add_argument("--train-draws", type=int, default=48)
+    ap.add_argument("--eval-draws", type=int, default=16)
+    ap.add_argument("--warm-tf", type=float, default=40.0)
+    ap.add_argument("--avg-tf", type=float, default=20.0)
+    ap.add_argument("--samples", type=int, default=80)
+    ap.add_argument("--iters", type=int, default=3000)
+    ap.add_argument("--run-tf", type=float, default=60.0)
+    ap.add_argument("--ref-tf", type=float, default=20.0)
+    ap.add_argument("--out", default="")
+    args = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    tr = draws(args.train_draws, seed=1)
+    Y, st = generate(tr, args.warm_tf, args.avg_tf, args.samples)
+    X = np.stack([features(Ra, Pr) for Ra, Pr, _ in tr])
+    keep = [k for k in range(len(tr)) if not st[k] and np.isfinite(Y[k]).all()]
+    t1 = time.time()
+    net = ConvNet(seed=0)
+    hist = train(net, X[keep], Y[keep], iters=args.iters)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    ev = evaluate(net, draws(args.eval_draws, seed=2), args.run_tf, args.ref_tf)
+    t3 = time.time()
+    res = {"train_draws": len(tr), "train_kept": len(keep), "loss": hist, "eval": ev,
+           "seconds": {"data": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}
+    both = [e for e in ev if e["steps_conductive"] and e["steps_warm"] and not e["diverged"]]
+    if both:
+        res["median_speedup"] = float(np.median([e["steps_conductive"] / e["steps_warm"] for e in both]))
+        res["warm_faster"] = sum(e["steps_warm"] < e["steps_conductive"] for e in both)
+        res["compared"] = len(both)
+    txt = json.dumps(res)
+    if args.out:
+        with open(args.out, "w") as fh:
+            fh.write(txt)
+    print(txt)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -81,6 +81,23 @@ _SIGS = {
                                    C.POINTER(C.c_int)]),
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "tlbm_init_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tlbm_conv3x3_pack_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "tlbm_conv3x3_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                       C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "tlbm_conv3x3_backward_data": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_int, C.c_void_p, C.c_void_p]),
+    "tlbm_conv3x3_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "tlbm_conv3x3_backward_weight": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                               C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
+                                               C.c_void_p]),
+    "tlbm_relu_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tlbm_to_bf16": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]),
+    "tlbm_mse_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p]),
+    "tlbm_adam_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_float, C.c_float,
+                                 C.c_float, C.c_float, C.c_int, C.c_void_p]),
+    "tlbm_upsample_bilinear": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "tlbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int, C.c_int,
                                     C.POINTER(tlbm_params)]),
     "tlbm_batch_required_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -233,6 +250,68 @@ def tlbm_derived(h) -> list:
 
 def tlbm_set_variant(h, vec=0, form=0, block_x=0, block_y=0):
     _check(h, lib().tlbm_set_variant(h, int(vec), int(form), int(block_x), int(block_y)))
+
+
+def tlbm_init_fields(h, T, ux=None, uy=None, uz=None):
+    """Warm start from device FP32 tensors of nx*ny*nz values."""
+    _check(h, lib().tlbm_init_fields(h, _ptr(T), _ptr(ux), _ptr(uy), _ptr(uz)))
+
+
+def _cs(stream):
+    return C.c_void_p(stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else 0))
+
+
+def _c(rc):
+    if rc != TLBM_OK:
+        raise TlbmError(rc, "invalid arguments or CUDA failure")
+
+
+def tlbm_conv3x3_pack_weights(w, cout, cin, a, stream=None):
+    _c(lib().tlbm_conv3x3_pack_weights(_ptr(w), cout, cin, _ptr(a), _cs(stream)))
+
+
+def tlbm_conv3x3_forward(x, a, bias, y, y_act, B, cin, cout, H, W, relu, stream=None):
+    _c(lib().tlbm_conv3x3_forward(_ptr(x), _ptr(a), _ptr(bias), _ptr(y), _ptr(y_act), B, cin, cout, H, W,
+                                  int(relu), _cs(stream)))
+
+
+def tlbm_conv3x3_backward_data(dy, w_bf16, dx, B, cin, cout, H, W, at_workspace, stream=None):
+    _c(lib().tlbm_conv3x3_backward_data(_ptr(dy), _ptr(w_bf16), _ptr(dx), B, cin, cout, H, W, _ptr(at_workspace),
+                                        _cs(stream)))
+
+
+def tlbm_conv3x3_workspace_bytes(B, cin, cout, H, W) -> int:
+    n = C.c_size_t()
+    _c(lib().tlbm_conv3x3_workspace_bytes(B, cin, cout, H, W, C.byref(n)))
+    return n.value
+
+
+def tlbm_conv3x3_backward_weight(x, dy_bf16, dy, dw, db, B, cin, cout, H, W, workspace, stream=None):
+    _c(lib().tlbm_conv3x3_backward_weight(_ptr(x), _ptr(dy_bf16), _ptr(dy), _ptr(dw), _ptr(db), B, cin, cout, H, W,
+                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                          _cs(stream)))
+
+
+def tlbm_relu_backward(dx, y, n, g, g_bf16, stream=None):
+    _c(lib().tlbm_relu_backward(_ptr(dx), _ptr(y), int(n), _ptr(g), _ptr(g_bf16), _cs(stream)))
+
+
+def tlbm_to_bf16(a, n, b, stream=None):
+    _c(lib().tlbm_to_bf16(_ptr(a), int(n), _ptr(b), _cs(stream)))
+
+
+def tlbm_mse_loss(y, target, n, g, g_bf16, loss_dev, partial_dev, stream=None):
+    _c(lib().tlbm_mse_loss(_ptr(y), _ptr(target), int(n), _ptr(g), _ptr(g_bf16), _ptr(loss_dev), _ptr(partial_dev),
+                           _cs(stream)))
+
+
+def tlbm_adam_step(w, g, m, v, n, lr, b1, b2, eps, t, stream=None):
+    _c(lib().tlbm_adam_step(_ptr(w), _ptr(g), _ptr(m), _ptr(v), int(n), float(lr), float(b1), float(b2), float(eps),
+                            int(t), _cs(stream)))
+
+
+def tlbm_upsample_bilinear(x, channels, h, w, factor, out, stream=None):
+    _c(lib().tlbm_upsample_bilinear(_ptr(x), channels, h, w, factor, _ptr(out), _cs(stream)))
 
 
 def tlbm_set_staged(h, tile_width=0, stages=0):

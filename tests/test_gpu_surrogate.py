@@ -1,0 +1,157 @@
+"""Learned warm start: the convolution, gradient, loss, optimiser, upsampling
+and warm-start kernels (through the C ABI) against the FP64 CPU oracle, and a
+short training run that fits."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import conv_oracle as CO
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_03160_gb300 import tlbm
+
+    tlbm.lib()
+    return tlbm
+
+
+def _bf16(a):
+    import torch
+
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+def _np(t):
+    import torch
+
+    return t.float().cpu().numpy().astype(np.float64) if t.dtype == torch.bfloat16 else t.cpu().numpy().astype(np.float64)
+
+
+SHAPES = [(2, 5, 32, 13, 11), (3, 32, 32, 9, 17), (1, 32, 3, 65, 65), (2, 7, 5, 4, 3)]
+
+
+@pytest.mark.parametrize("B,cin,cout,H,W", SHAPES)
+def test_conv_forward_backward_match_oracle(T, B, cin, cout, H, W):
+    import torch
+
+    s = torch.cuda.current_stream()
+    x = _bf16(inputs.uniform_array(1 + cin, (B, cin, H, W), -1, 1)).cuda()
+    w32 = torch.tensor(inputs.uniform_array(2 + cin, (cout, cin, 3, 3), -0.3, 0.3), dtype=torch.float32).cuda()
+    bias = torch.tensor(inputs.uniform_array(3, (cout,), -0.1, 0.1), dtype=torch.float32).cuda()
+    kp = (cin * 9 + 15) // 16 * 16
+    a = torch.empty((cout, kp), dtype=torch.bfloat16, device="cuda")
+    T.tlbm_conv3x3_pack_weights(w32, cout, cin, a, s)
+    w16 = w32.to(torch.bfloat16)
+    y = torch.empty((B, cout, H, W), dtype=torch.float32, device="cuda")
+    act = torch.empty((B, cout, H, W), dtype=torch.bfloat16, device="cuda")
+    T.tlbm_conv3x3_forward(x, a, bias, y, act, B, cin, cout, H, W, 1, s)
+    xr, wr = _np(x), _np(w16)
+    ref = CO.conv3x3(xr, wr, _np(bias))
+    scale = np.abs(ref).max()
+    assert np.abs(_np(y) - ref).max() <= 1e-5 * scale
+    assert np.abs(_np(act) - np.maximum(_np(y), 0)).max() <= 8e-3 * scale
+
+    dy32 = torch.tensor(inputs.uniform_array(4, (B, cout, H, W), -1, 1), dtype=torch.float32).cuda()
+    dy16 = dy32.to(torch.bfloat16)
+    dyr = _np(dy16)
+    rdx, rdw, rdb = CO.conv3x3_backward(xr, wr, dyr)
+    dx = torch.empty((B, cin, H, W), dtype=torch.float32, device="cuda")
+    at = torch.empty(32 * 288, dtype=torch.bfloat16, device="cuda")
+    T.tlbm_conv3x3_backward_data(dy16, w16, dx, B, cin, cout, H, W, at, s)
+    assert np.abs(_np(dx) - rdx).max() <= 1e-5 * np.abs(rdx).max()
+    ws = torch.empty(T.tlbm_conv3x3_workspace_bytes(B, cin, cout, H, W), dtype=torch.uint8, device="cuda")
+    dw = torch.empty((cout, cin, 3, 3), dtype=torch.float32, device="cuda")
+    db = torch.empty(cout, dtype=torch.float32, device="cuda")
+    T.tlbm_conv3x3_backward_weight(x, dy16, dy32, dw, db, B, cin, cout, H, W, ws, s)
+    assert np.abs(_np(dw) - rdw).max() <= 1e-5 * np.abs(rdw).max()
+    assert np.abs(_np(db) - _np(dy32).sum(axis=(0, 2, 3))).max() <= 1e-5 * max(1.0, np.abs(rdb).max())
+    # deterministic: the same call twice gives the same bits
+    dw2 = torch.empty_like(dw)
+    T.tlbm_conv3x3_backward_weight(x, dy16, dy32, dw2, db, B, cin, cout, H, W, ws, s)
+    assert torch.equal(dw, dw2)
+
+
+def test_loss_relu_adam_upsample_match_oracle(T):
+    import torch
+
+    s = torch.cuda.current_stream()
+    n = 3 * 65 * 65
+    y = torch.tensor(inputs.uniform_array(5, (n,), -1, 1), dtype=torch.float32).cuda()
+    t = torch.tensor(inputs.uniform_array(6, (n,), -1, 1), dtype=torch.float32).cuda()
+    g32 = torch.empty_like(y)
+    g16 = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    part = torch.zeros(1024, dtype=torch.float64, device="cuda")
+    T.tlbm_mse_loss(y, t, n, g32, g16, loss, part, s)
+    rl, rg = CO.mse(_np(y), _np(t))
+    # the difference y - t is formed in FP32, its square summed in FP64
+    assert abs(loss.item() - rl) < 1e-7 * rl and np.abs(_np(g32) - rg).max() < 1e-9
+
+    dx = torch.tensor(inputs.uniform_array(7, (n,), -1, 1), dtype=torch.float32).cuda()
+    g = torch.empty_like(dx)
+    gh = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    T.tlbm_relu_backward(dx, y, n, g, gh, s)
+    assert np.array_equal(_np(g), _np(dx) * (_np(y) > 0))
+
+    w = torch.tensor(inputs.uniform_array(8, (100,), -1, 1), dtype=torch.float32).cuda()
+    gr = torch.tensor(inputs.uniform_array(9, (100,), -1, 1), dtype=torch.float32).cuda()
+    m = torch.zeros(100, device="cuda")
+    v = torch.zeros(100, device="cuda")
+    wr, mr, vr = _np(w), np.zeros(100), np.zeros(100)
+    for it in (1, 2, 3):
+        T.tlbm_adam_step(w, gr, m, v, 100, 1e-2, 0.9, 0.999, 1e-8, it, s)
+        wr, mr, vr = CO.adam(wr, _np(gr), mr, vr, it, 1e-2)
+    assert np.abs(_np(w) - wr).max() < 1e-6
+
+    c = torch.tensor(inputs.uniform_array(10, (3, 9, 7), -1, 1), dtype=torch.float32).cuda()
+    out = torch.empty((3, 65, 49), dtype=torch.float32, device="cuda")
+    T.tlbm_upsample_bilinear(c, 3, 9, 7, 8, out, s)
+    assert np.abs(_np(out) - CO.upsample_bilinear_vertex(_np(c), 8)).max() < 1e-6
+
+
+def test_warm_start_state_matches_oracle(T, O):
+    """tlbm_init_fields: f = f_eq(1, u), g = g_eq(T, u) at every node."""
+    import torch
+
+    nx, ny = 21, 17
+    g = T.Sim(nx, ny, lattice=0, Ra=1e6, Pr=0.71, Ma=0.1, precision=0)
+    Tf = inputs.uniform_array(11, (ny, nx), -0.5, 0.5)
+    ux = inputs.uniform_array(12, (ny, nx), -0.05, 0.05)
+    uy = inputs.uniform_array(13, (ny, nx), -0.05, 0.05)
+    dev = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda").contiguous()
+    T.tlbm_init_fields(g.h, dev(Tf), dev(ux), dev(uy), None)
+    f, gg = g.get_populations()
+    o = O.Sim(nx, ny, Ra=1e6, Pr=0.71, Ma=0.1)
+    a_T = o.derived()["a_T"]
+    e, w, _, M, Mi = O.velocity_set(0)
+    T32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    for j in (0, 5, ny - 1):
+        for i in (0, 7, nx - 1):
+            u = [T32(ux)[j, i], T32(uy)[j, i], 0.0]
+            assert np.abs(f[:, j, i] - Mi @ O.flow_meq(0, 1.0, u)).max() < 1e-15
+            assert np.abs(gg[:, j, i] - O.thermal_geq(0, a_T, T32(Tf)[j, i], u)).max() < 1e-15
+
+
+def test_short_training_fits(T):
+    """Full-batch Adam on the project's kernels fits a smooth target field."""
+    import torch
+
+    from paper_2211_03160_gb300 import surrogate as S
+
+    rng = np.random.default_rng(3)
+    X = np.stack([S.features(10 ** rng.uniform(6, 8), rng.choice([0.71, 7.0])) for _ in range(6)])
+    yy, xx = np.meshgrid(np.linspace(0, 1, 65), np.linspace(0, 1, 65), indexing="ij")
+    Y = np.stack([np.stack([X[k, 0] + 0.05 * np.sin(np.pi * xx) * X[k, 3], 0.2 * np.sin(np.pi * xx) * np.sin(np.pi * yy),
+                            -0.1 * np.sin(2 * np.pi * xx) * yy]) for k in range(6)]).astype(np.float32)
+    net = S.ConvNet(seed=1)
+    hist = S.train(net, X, Y, iters=300, lr=3e-3, log_every=100)
+    assert hist[-1][1] < 0.1 * hist[0][1], hist
+    pred = S.predict(net, 1e7, 0.71)
+    assert pred.shape == (3, 65, 65) and torch.isfinite(pred).all()
