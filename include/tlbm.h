@@ -148,8 +148,15 @@ TLBM_API int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp);
  * required; a NULL velocity component is 0.  Asynchronous. */
 TLBM_API int tlbm_init_fields(tlbm_t h, const float* T, const float* ux, const float* uy, const float* uz);
 
-/* Advance n >= 0 time steps (Eqs. (10)-(11), fused).  Asynchronous. */
+/* Advance n >= 0 time steps (Eqs. (10)-(11), fused).  Asynchronous.  Whole
+ * blocks of graph_steps steps (tlbm_set_graph, default 16) are replayed from a
+ * CUDA graph captured at the first such block; the rest are plain launches. */
 TLBM_API int tlbm_step(tlbm_t h, int64_t n);
+
+/* Steps per CUDA graph replay in tlbm_step (even, <= 4096; 0 = plain launches
+ * only).  The graph is captured on a private stream the first time it is needed
+ * and dropped when the variant, the staged setting or the bound memory change. */
+TLBM_API int tlbm_set_graph(tlbm_t h, int steps);
 
 /* Macroscopic fields of the current state into caller device arrays of
  * nx*ny*nz elements (x fastest), element type out_dtype.  NULL skips a field;
@@ -189,12 +196,15 @@ TLBM_API int tlbm_status(tlbm_t h, int* diverged, int64_t* step);
 TLBM_API int tlbm_derived(tlbm_t h, double* out, int cap, int* count);
 
 /* Choose the step kernel variant: vec = nodes per thread (0 = default),
+ * rows = consecutive rows per thread (0 or 1: one; 2 or 4: software-pipelined,
+ * the next row's loads are issued before the current row is collided; those
+ * variants exist for the two-relaxation-time form),
  * form = 0 automatic (two-relaxation-time evaluation when the rates allow it,
  * else the general MRT), 1 general MRT, 2 two-relaxation-time (TLBM_ERR_ARG if
  * the rates are not of that form); block_x (multiple of 32) x block_y threads
  * per block (0 = the tuned default of the lattice and precision).  All variants compute the same collision;
  * TLBM_ERR_UNSUPPORTED if the variant is not compiled. */
-TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y);
+TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y, int rows);
 /* Use the shared-memory staged step kernel instead: a persistent grid whose
  * blocks copy each tile's source rows (one row segment of tile_width nodes per
  * population) into shared memory with TMA bulk copies completing on mbarriers,
@@ -206,7 +216,7 @@ TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bloc
 TLBM_API int tlbm_set_staged(tlbm_t h, int tile_width, int stages);
 /* Current variant (form reported as 1 MRT or 2 TRT; vec 0 for the staged
  * kernel).  Outputs may be NULL. */
-TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y);
+TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y, int* rows);
 
 /* ---------------------------------------------------------------- batched ensemble
  * n independent cells with their own sizes, (Ra, Pr, Ma) and seeds, one lattice

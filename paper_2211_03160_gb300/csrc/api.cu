@@ -46,6 +46,8 @@ static int cuda_fail(tlbm_t h, cudaError_t e, const char* what) {
     return fail(h, TLBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+static void drop_graph(tlbm_t h);
+
 #define TLBM_CHECK_HANDLE(h)                                   \
     do {                                                       \
         if (!(h)) return fail(nullptr, TLBM_ERR_ARG, "NULL handle"); \
@@ -410,20 +412,20 @@ static double pick(double v, double d) { return std::isnan(v) ? d : v; }
 // Default step variant per (dimension, storage): nodes per thread and block
 // shape, from a sweep on GB300 at 8193^2 (2D) and 385^3 (3D).
 struct VariantDefault {
-    int vec, bx, by;
+    int vec, bx, by, rows;
 };
 static VariantDefault default_variant(int dim, int prec) {
     if (dim == 2) {
         switch (prec) {
-        case TLBM_FP64: return {2, 64, 1};
-        case TLBM_FP32: return {4, 32, 1};
-        default: return {4, 32, 4};
+        case TLBM_FP64: return {2, 64, 1, 1};
+        case TLBM_FP32: return {4, 32, 1, 1};
+        default: return {4, 32, 4, 1};
         }
     }
     switch (prec) {
-    case TLBM_FP64: return {1, 32, 4};
-    case TLBM_FP32: return {1, 32, 2};
-    default: return {1, 32, 8};
+    case TLBM_FP64: return {1, 32, 4, 1};
+    case TLBM_FP32: return {1, 32, 2, 1};
+    default: return {1, 32, 8, 1};
     }
 }
 static int default_vec(int dim, int prec) { return default_variant(dim, prec).vec; }
@@ -558,6 +560,7 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
     h->vec = default_variant(dim, precision).vec;
     h->bx = default_variant(dim, precision).bx;
     h->by = default_variant(dim, precision).by;
+    h->rows = default_variant(dim, precision).rows;
     kp.xmax_load = kp.L.P - h->vec;
     kp.gbeta = h->gbeta; kp.omega = h->omega; kp.Th = h->prm.Th; kp.Tc = h->prm.Tc; kp.a_T = h->a_T;
     for (int a = 0; a < 3; ++a) {
@@ -603,6 +606,7 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
     h->stream = nullptr;
     h->cur = 0;
     h->t = 0;
+    h->graph_steps = 16;
     *out = h;
     return TLBM_OK;
 }
@@ -628,6 +632,7 @@ extern "C" int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes) {
     // the staged kernel's status word starts cleared
     e = cudaMemset((char*)dev_ptr + h->status_off, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
+    drop_graph(h);
     h->mem = (char*)dev_ptr;
     h->mem_bytes = bytes;
     h->buf[0] = h->mem;
@@ -675,8 +680,12 @@ extern "C" int tlbm_init_fields(tlbm_t h, const float* T, const float* ux, const
     return TLBM_OK;
 }
 
-static cudaError_t launch_one_step(tlbm_t h) {
+// Launch one step reading buffer `parity` and writing the other, on stream s
+// (no bookkeeping).
+static cudaError_t launch_step_raw(tlbm_t h, int parity, cudaStream_t s) {
     const KParams& kp = h->kp;
+    const void* src = h->buf[parity];
+    void* dst = h->buf[parity ^ 1];
     if (h->staged) {
         const int A = 16 / (int)h->elem;
         StagedInfo si;
@@ -686,23 +695,51 @@ static cudaError_t launch_one_step(tlbm_t h) {
         si.lw = si.tw + 2 * A;
         si.stages = h->staged_stages;
         si.status = (int*)(h->mem + h->status_off);
-        cudaError_t e = launch_staged(h->dim, h->prec, h->buf[h->cur], h->buf[h->cur ^ 1], kp, si, h->staged_grid,
-                                      h->staged_smem, h->stream);
-        if (e == cudaSuccess) {
-            h->cur ^= 1;
-            h->t += 1;
-            h->launches += 1;
-        }
-        return e;
+        return launch_staged(h->dim, h->prec, src, dst, kp, si, h->staged_grid, h->staged_smem, s);
     }
     const int vec = h->vec;
-    const int bx = h->bx, by = h->by;
+    const int bx = h->bx, by = h->by, rows = h->rows;
     const int threads_x = (h->nx + vec - 1) / vec;
     dim3 block(bx, by, 1);
-    dim3 grid((threads_x + bx - 1) / bx, (h->ny + by - 1) / by, h->dim == 3 ? h->nz : 1);
-    const void* src = h->buf[h->cur];
-    void* dst = h->buf[h->cur ^ 1];
-    cudaError_t e = launch_step(h->dim, h->prec, vec, h->trt != 0, src, dst, kp, grid, block, h->stream);
+    dim3 grid((threads_x + bx - 1) / bx, (h->ny + by * rows - 1) / (by * rows), h->dim == 3 ? h->nz : 1);
+    return launch_step(h->dim, h->prec, vec, h->trt != 0, rows, src, dst, kp, grid, block, s);
+}
+
+static void drop_graph(tlbm_t h) {
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
+
+// Capture graph_steps steps starting from buffer 0 into a CUDA graph (on a
+// private stream; the graph is replayed on the handle's stream).
+static int build_graph(tlbm_t h) {
+    drop_graph(h);
+    cudaError_t e = cudaSuccess;
+    if (!h->capture_stream) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
+    e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < h->graph_steps && le == cudaSuccess; ++k) le = launch_step_raw(h, k & 1, h->capture_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->capture_stream, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, le != cudaSuccess ? le : e, "step graph capture");
+    }
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    return TLBM_OK;
+}
+
+static cudaError_t launch_one_step(tlbm_t h) {
+    cudaError_t e = launch_step_raw(h, h->cur, h->stream);
     if (e == cudaSuccess) {
         h->cur ^= 1;
         h->t += 1;
@@ -715,10 +752,31 @@ extern "C" int tlbm_step(tlbm_t h, int64_t n) {
     TLBM_CHECK_HANDLE(h);
     TLBM_CHECK_BOUND(h);
     if (n < 0) return fail(h, TLBM_ERR_ARG, "n must be >= 0");
-    for (int64_t i = 0; i < n; ++i) {
-        cudaError_t e = launch_one_step(h);
-        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    while (n > 0) {
+        if (h->graph_steps >= 2 && h->cur == 0 && n >= h->graph_steps) {
+            if (!h->graph) {
+                int rc = build_graph(h);
+                if (rc != TLBM_OK) return rc;
+            }
+            cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+            h->t += h->graph_steps;  // an even number of steps: the state is back in buffer 0
+            h->launches += h->graph_steps;
+            n -= h->graph_steps;
+        } else {
+            cudaError_t e = launch_one_step(h);
+            if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+            n -= 1;
+        }
     }
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_set_graph(tlbm_t h, int steps) {
+    TLBM_CHECK_HANDLE(h);
+    if (steps < 0 || steps % 2 || steps > 4096) return fail(h, TLBM_ERR_ARG, "steps must be even, in [0, 4096]");
+    drop_graph(h);
+    h->graph_steps = steps;
     return TLBM_OK;
 }
 
@@ -867,7 +925,7 @@ extern "C" int tlbm_set_populations(tlbm_t h, const double* host_f, const double
     return TLBM_OK;
 }
 
-extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y) {
+extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y, int rows) {
     TLBM_CHECK_HANDLE(h);
     const int v = vec > 0 ? vec : default_vec(h->dim, h->prec);
     if (form < 0 || form > 2) return fail(h, TLBM_ERR_ARG, "form must be 0 (auto), 1 (MRT) or 2 (TRT)");
@@ -877,10 +935,12 @@ extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bl
     const int bx = block_x > 0 ? block_x : default_variant(h->dim, h->prec).bx;
     const int by = block_y > 0 ? block_y : default_variant(h->dim, h->prec).by;
     if (bx % 32 || bx * by > 1024) return fail(h, TLBM_ERR_ARG, "block_x must be a multiple of 32, bx*by <= 1024");
-    if (!step_variant_available(h->dim, h->prec, v, trt != 0))
-        return fail(h, TLBM_ERR_UNSUPPORTED, "step variant (vec %d, %s) not built", v, trt ? "TRT" : "MRT");
+    const int nr = rows > 0 ? rows : 1;
+    if (!step_variant_available(h->dim, h->prec, v, trt != 0, nr))
+        return fail(h, TLBM_ERR_UNSUPPORTED, "step variant (vec %d, %s, %d rows) not built", v, trt ? "TRT" : "MRT",
+                    nr);
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, step_function(h->dim, h->prec, v, trt != 0));
+    cudaError_t e = cudaFuncGetAttributes(&fa, step_function(h->dim, h->prec, v, trt != 0, nr));
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncGetAttributes");
     if (bx * by > fa.maxThreadsPerBlock)
         return fail(h, TLBM_ERR_ARG, "block of %d threads exceeds the variant's limit of %d", bx * by,
@@ -889,8 +949,10 @@ extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bl
     h->trt = trt;
     h->bx = bx;
     h->by = by;
+    h->rows = nr;
     h->staged = 0;
     h->kp.xmax_load = h->kp.L.P - v;
+    drop_graph(h);
     return TLBM_OK;
 }
 
@@ -927,11 +989,13 @@ extern "C" int tlbm_set_staged(tlbm_t h, int tile_width, int stages) {
     h->staged_stages = ns;
     h->staged_smem = smem;
     h->staged_grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
+    drop_graph(h);
     return TLBM_OK;
 }
 
-extern "C" int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y) {
+extern "C" int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y, int* rows) {
     TLBM_CHECK_HANDLE(h);
+    if (rows) *rows = h->rows;
     if (vec) *vec = h->staged ? 0 : h->vec;
     if (form) *form = h->trt ? 2 : 1;
     if (block_x) *block_x = h->bx;
@@ -962,4 +1026,9 @@ extern "C" int tlbm_launch_count(tlbm_t h, int64_t* count) {
     return TLBM_OK;
 }
 
-extern "C" void tlbm_destroy(tlbm_t h) { delete h; }
+extern "C" void tlbm_destroy(tlbm_t h) {
+    if (!h) return;
+    drop_graph(h);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    delete h;
+}

@@ -144,7 +144,7 @@ static void drop_graph(tlbm_batch_t b) {
 // batch's compiled set
 static void batch_default_variant(tlbm_batch_t b) {
     int v = 0, form = 0, bx = 0, by = 0;
-    tlbm_get_variant(b->inst[0], &v, &form, &bx, &by);
+    tlbm_get_variant(b->inst[0], &v, &form, &bx, &by, nullptr);
     b->vec = v;
     b->trt = 1;
     for (tlbm_t h : b->inst) b->trt = b->trt && h->kp.trt;

@@ -15,6 +15,10 @@ struct tlbm_s {
     double S[tlbm::MAXQ], Q[7];
     tlbm::KParams kp;
     int vec, trt, bx, by;      // step kernel variant and block shape
+    int rows;                  // consecutive rows per thread (software-pipelined when > 1)
+    int graph_steps;           // steps per CUDA graph replay in tlbm_step (0: plain launches)
+    cudaGraphExec_t graph;     // captured block of graph_steps steps starting from buffer 0
+    cudaStream_t capture_stream;
     int staged;                // 1: shared-memory staged (TMA bulk copy) kernel
     int staged_tw, staged_stages, staged_grid;
     size_t staged_smem;

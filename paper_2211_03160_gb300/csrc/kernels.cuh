@@ -735,6 +735,187 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
     }
 }
 
+// ------------------------------------------------------------------ software-pipelined rows
+
+// The raw stored values one thread pulls for one row: the aligned vector of
+// every population and, for the warp's edge lane, the one element beyond it.
+template <int DIM, class S, int VEC>
+struct RawRow {
+    static constexpr int Q = Lat<DIM>::F::Q + Lat<DIM>::G::Q;
+    S v[Q][VEC];
+    S h[Q];
+};
+
+// Issue the loads of one row (no use of the loaded values yet).
+template <int DIM, class S, int VEC>
+__device__ __forceinline__ void fetch_row(const S* __restrict__ own, const KParams& p, int lane,
+                                          RawRow<DIM, S, VEC>& r) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    static_for<LF::Q + LG::Q>([&](auto jj) {
+        constexpr int j = decltype(jj)::value;
+        constexpr int ex = j < LF::Q ? LF::e(j < LF::Q ? j : 0, 0) : LG::e(j < LF::Q ? 0 : j - LF::Q, 0);
+        const S* __restrict__ q = own + p.loff[j];
+        if constexpr (VEC == 1) {
+            r.v[j][0] = q[-ex];
+        } else {
+            ld_vec<S, VEC>(q, r.v[j]);
+            if constexpr (ex == 1) {
+                if (lane == 0) r.h[j] = q[-1];
+            } else if constexpr (ex == -1) {
+                if (lane == 31) r.h[j] = q[VEC];
+            }
+        }
+    });
+}
+
+// Shift, convert and decode a fetched row (all 32 lanes together).
+template <int DIM, class S, int VEC, class C, bool KS>
+__device__ __forceinline__ void decode_row(const RawRow<DIM, S, VEC>& r, const KParams& p, int lane,
+                                           C (&f)[Lat<DIM>::F::Q][VEC], C (&g)[Lat<DIM>::G::Q][VEC]) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    const C inv_scale = ScaleOf<C>::inv(p);
+    static_for<LF::Q + LG::Q>([&](auto jj) {
+        constexpr int j = decltype(jj)::value;
+        constexpr bool flow = j < LF::Q;
+        constexpr int ex = flow ? LF::e(flow ? j : 0, 0) : LG::e(flow ? 0 : j - LF::Q, 0);
+        C t[VEC];
+        if constexpr (VEC == 1 || ex == 0) {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) t[k] = to_c<C>(r.v[j][k]);
+        } else if constexpr (ex == 1) {
+            C left = __shfl_up_sync(0xffffffffu, to_c<C>(r.v[j][VEC - 1]), 1);
+            if (lane == 0) left = to_c<C>(r.h[j]);
+            t[0] = left;
+#pragma unroll
+            for (int k = 1; k < VEC; ++k) t[k] = to_c<C>(r.v[j][k - 1]);
+        } else {
+            C right = __shfl_down_sync(0xffffffffu, to_c<C>(r.v[j][0]), 1);
+            if (lane == 31) right = to_c<C>(r.h[j]);
+#pragma unroll
+            for (int k = 0; k < VEC - 1; ++k) t[k] = to_c<C>(r.v[j][k + 1]);
+            t[VEC - 1] = right;
+        }
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            if constexpr (flow) f[j][k] = raw_to_dev_k<LF, S, C, KS>(t[k], j, inv_scale);
+            else g[j - LF::Q][k] = raw_to_g_k<S, C, KS>(t[k], inv_scale);
+        }
+    });
+}
+
+// Collide and store one decoded row (all lanes participate; stores predicated).
+template <int DIM, class S, int VEC, bool TRT, class C, bool KS>
+__device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p, int x0, int y, int z,
+                                           long long row, C (&f)[Lat<DIM>::F::Q][VEC],
+                                           C (&g)[Lat<DIM>::G::Q][VEC]) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    constexpr int QF = LF::Q, QG = LG::Q;
+    const Layout& L = p.L;
+    const C scale = ScaleOf<C>::s(p);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        C fd[QF], gd[QG];
+#pragma unroll
+        for (int i = 0; i < QF; ++i) fd[i] = f[i][k];
+#pragma unroll
+        for (int i = 0; i < QG; ++i) gd[i] = g[i][k];
+        collide<DIM, TRT, C, KS>(fd, gd, p);
+#pragma unroll
+        for (int i = 0; i < QF; ++i) f[i][k] = fd[i];
+#pragma unroll
+        for (int i = 0; i < QG; ++i) g[i][k] = gd[i];
+    }
+    if (x0 >= L.nx) return;
+    S* __restrict__ own = dst + row + x0;
+    if (x0 + VEC <= L.nx) {
+        static_for<QF>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            S v[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+            st_vec<S, VEC>(own + p.soff[i], v);
+        });
+        static_for<QG>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            S v[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
+            st_vec<S, VEC>(own + p.soff[QF + i], v);
+        });
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            if (x0 + k < L.nx) {
+                static_for<QF>([&](auto ii) {
+                    constexpr int i = decltype(ii)::value;
+                    own[p.soff[i] + k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                });
+                static_for<QG>([&](auto ii) {
+                    constexpr int i = decltype(ii)::value;
+                    own[p.soff[QF + i] + k] = enc_g_k<S, C, KS>(g[i][k], scale);
+                });
+            }
+        }
+    }
+    const bool edge = (x0 == 0) || (x0 + VEC >= L.nx) || (y == 0) || (y == L.ny - 1) ||
+                      (DIM == 3 && (z == 0 || z == L.nz - 1));
+    if (edge) {
+        C post[(QF + QG) * VEC];
+        const C un = KS ? ScaleOf<C>::inv(p) : C(1);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+#pragma unroll
+            for (int i = 0; i < QF; ++i) post[i * VEC + k] = KS ? f[i][k] * un : f[i][k];
+#pragma unroll
+            for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = KS ? g[i][k] * un : g[i][k];
+        }
+        edge_writes<DIM, S, VEC, C>(dst, p, x0, y, z, post);
+    }
+}
+
+// ROWS consecutive rows per thread, software-pipelined: the loads of the next
+// row are issued before the current row is collided, so every warp keeps loads
+// in flight while it computes.
+template <int DIM, class S, int VEC, bool TRT, int ROWS>
+__global__ void step_kernel_rows(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
+    using C = typename Storage<S>::C;
+    constexpr int QF = Lat<DIM>::F::Q, QG = Lat<DIM>::G::Q;
+    constexpr bool KS = TRT && Storage<S>::offset;
+    const Layout& L = p.L;
+    const int lane = threadIdx.x & 31;
+    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * ROWS;
+    const int z = DIM == 3 ? (int)blockIdx.z : 0;
+    if (y0 >= L.ny) return;  // uniform across the warp
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
+    if (x0 - lane * VEC >= L.nx) return;  // the whole warp lies past the row end
+    const int x0ld = min(x0, p.xmax_load);
+    const long long row0 = L.row(y0, z);
+    RawRow<DIM, S, VEC> A, B;
+    fetch_row<DIM, S, VEC>(src + row0 + x0ld, p, lane, A);
+#pragma unroll
+    for (int r = 0; r < ROWS; r += 2) {
+        const int ya = y0 + r, yb = ya + 1;
+        const long long rowa = row0 + (long long)r * L.P;
+        if (r + 1 < ROWS && yb < L.ny) fetch_row<DIM, S, VEC>(src + rowa + L.P + x0ld, p, lane, B);
+        {
+            C f[QF][VEC], g[QG][VEC];
+            decode_row<DIM, S, VEC, C, KS>(A, p, lane, f, g);
+            finish_row<DIM, S, VEC, TRT, C, KS>(dst, p, x0, ya, z, rowa, f, g);
+        }
+        if (r + 1 >= ROWS || yb >= L.ny) break;
+        if (r + 2 < ROWS && yb + 1 < L.ny) fetch_row<DIM, S, VEC>(src + rowa + 2 * L.P + x0ld, p, lane, A);
+        {
+            C f[QF][VEC], g[QG][VEC];
+            decode_row<DIM, S, VEC, C, KS>(B, p, lane, f, g);
+            finish_row<DIM, S, VEC, TRT, C, KS>(dst, p, x0, yb, z, rowa + L.P, f, g);
+        }
+        if (yb + 1 >= L.ny) break;
+    }
+}
+
 template <int DIM, class S, int VEC, bool TRT>
 __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
     step_block<DIM, S, VEC, TRT>(src, dst, p, blockIdx.x, blockIdx.y, blockIdx.z);

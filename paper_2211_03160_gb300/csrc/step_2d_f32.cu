@@ -2,20 +2,24 @@
 #include "dispatch.h"
 
 namespace tlbm {
-cudaError_t launch_step_2d_f32(int vec, bool trt, const void* src, void* dst, const KParams& p, dim3 grid,
+cudaError_t launch_step_2d_f32(int vec, bool trt, int rows, const void* src, void* dst, const KParams& p, dim3 grid,
                         dim3 block, cudaStream_t s) {
     TLBM_STEP_CASE(2, float, 4, true)
     TLBM_STEP_CASE(2, float, 2, true)
     TLBM_STEP_CASE(2, float, 1, true)
     TLBM_STEP_CASE(2, float, 4, false)
+    TLBM_ROWS_CASE(2, float, 4, 2)
+    TLBM_ROWS_CASE(2, float, 4, 4)
     return cudaErrorInvalidValue;
 }
 
-const void* func_step_2d_f32(int vec, bool trt) {
+const void* func_step_2d_f32(int vec, bool trt, int rows) {
     TLBM_STEP_FUNC(2, float, 4, true)
     TLBM_STEP_FUNC(2, float, 2, true)
     TLBM_STEP_FUNC(2, float, 1, true)
     TLBM_STEP_FUNC(2, float, 4, false)
+    TLBM_ROWS_FUNC(2, float, 4, 2)
+    TLBM_ROWS_FUNC(2, float, 4, 4)
     return nullptr;
 }
 }  // namespace tlbm

@@ -276,6 +276,7 @@ def evaluate(net: ConvNet, draw_list, run_tf: float, ref_tf: float, samples_per_
     status = b.status()
     b.close()
     window = samples_per_tf // 2  # half a free-fall time
+    series = {"dt": dt, "samples_per_tf": samples_per_tf, "nu": np.round(nus, 5).tolist()}
     out = []
     ref_samples = int(ref_tf * samples_per_tf)
     for k, (Ra, Pr, seed) in enumerate(draw_list):
@@ -284,7 +285,7 @@ def evaluate(net: ConvNet, draw_list, run_tf: float, ref_tf: float, samples_per_
         warm = steps_to_steady(nus[n + k], dt, window, ref)
         out.append({"Ra": Ra, "Pr": Pr, "Nu_ref": ref, "steps_conductive": cold, "steps_warm": warm,
                     "diverged": bool(status[k] or status[n + k])})
-    return out
+    return out, series
 
 
 def main(argv=None):
@@ -300,11 +301,19 @@ def main(argv=None):
     ap.add_argument("--run-tf", type=float, default=60.0)
     ap.add_argument("--ref-tf", type=float, default=20.0)
     ap.add_argument("--out", default="")
+    ap.add_argument("--save-data", default="", help="write the generated training targets (.npz)")
+    ap.add_argument("--load-data", default="", help="reuse training targets written by --save-data")
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
     t0 = time.time()
     tr = draws(args.train_draws, seed=1)
-    Y, st = generate(tr, args.warm_tf, args.avg_tf, args.samples)
+    if args.load_data:
+        z = np.load(args.load_data)
+        Y, st = z["Y"], list(z["status"])
+    else:
+        Y, st = generate(tr, args.warm_tf, args.avg_tf, args.samples)
+    if args.save_data:
+        np.savez(args.save_data, Y=Y, status=np.array(st))
     X = np.stack([features(Ra, Pr) for Ra, Pr, _ in tr])
     keep = [k for k in range(len(tr)) if not st[k] and np.isfinite(Y[k]).all()]
     t1 = time.time()
@@ -312,9 +321,9 @@ def main(argv=None):
     hist = train(net, X[keep], Y[keep], iters=args.iters)
     torch.cuda.synchronize()
     t2 = time.time()
-    ev = evaluate(net, draws(args.eval_draws, seed=2), args.run_tf, args.ref_tf)
+    ev, series = evaluate(net, draws(args.eval_draws, seed=2), args.run_tf, args.ref_tf)
     t3 = time.time()
-    res = {"train_draws": len(tr), "train_kept": len(keep), "loss": hist, "eval": ev,
+    res = {"train_draws": len(tr), "train_kept": len(keep), "loss": hist, "eval": ev, "series": series,
            "seconds": {"data": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}
     both = [e for e in ev if e["steps_conductive"] and e["steps_warm"] and not e["diverged"]]
     if both:

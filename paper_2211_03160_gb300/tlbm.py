@@ -76,11 +76,11 @@ _SIGS = {
                                               C.c_void_p, C.c_void_p]),
     "tlbm_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "tlbm_derived": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
-    "tlbm_set_variant": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
-    "tlbm_get_variant": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                   C.POINTER(C.c_int)]),
+    "tlbm_set_variant": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "tlbm_get_variant": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "tlbm_set_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "tlbm_init_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tlbm_conv3x3_pack_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "tlbm_conv3x3_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
@@ -314,6 +314,10 @@ def tlbm_upsample_bilinear(x, channels, h, w, factor, out, stream=None):
     _c(lib().tlbm_upsample_bilinear(_ptr(x), channels, h, w, factor, _ptr(out), _cs(stream)))
 
 
+def tlbm_set_graph(h, steps):
+    _check(h, lib().tlbm_set_graph(h, int(steps)))
+
+
 def tlbm_set_staged(h, tile_width=0, stages=0):
     _check(h, lib().tlbm_set_staged(h, int(tile_width), int(stages)))
 
@@ -451,8 +455,8 @@ class Sim:
         assert f.size == self.qf * self.N and g.size == self.qg * self.N
         tlbm_set_populations(self.h, f, g)
 
-    def set_variant(self, vec=0, form=0, block_x=0, block_y=0):
-        tlbm_set_variant(self.h, vec, form, block_x, block_y)
+    def set_variant(self, vec=0, form=0, block_x=0, block_y=0, rows=0):
+        tlbm_set_variant(self.h, vec, form, block_x, block_y, rows)
 
     def set_staged(self, tile_width=0, stages=0):
         tlbm_set_staged(self.h, tile_width, stages)

@@ -97,6 +97,12 @@ VARIANTS = {
     (D3, FP32): [(4, 2), (2, 2), (1, 2), (2, 1)], (D3, FP16): [(4, 2), (2, 2), (1, 2), (4, 1)],
     (D3, BF16): [(4, 2), (2, 2), (1, 2), (4, 1)], (D3, FP64): [(1, 2), (2, 2), (1, 1)],
 }
+# software-pipelined variants: (vec, rows), two-relaxation-time form
+ROW_VARIANTS = {
+    (D2, FP32): [(4, 2), (4, 4)], (D2, FP16): [(4, 2), (4, 4), (8, 2), (8, 4)],
+    (D2, BF16): [(4, 2), (4, 4), (8, 2), (8, 4)], (D2, FP64): [],
+    (D3, FP32): [(1, 2), (1, 4)], (D3, FP16): [(1, 2), (1, 4)], (D3, BF16): [(1, 2), (1, 4)], (D3, FP64): [],
+}
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32, FP16, BF16])
@@ -113,19 +119,20 @@ def test_one_step_random_populations(T, O, prec, lattice, shape, walls, pm):
     f = inputs.uniform_array(seed, (qf,) + o.shape, 0.02, 0.2)
     gg = inputs.uniform_array(seed + 1, (qg,) + o.shape, -0.1, 0.1)
     ref = None
-    variants = list(VARIANTS[(lattice, prec)])
+    variants = [("reg", v, f, 1) for v, f in VARIANTS[(lattice, prec)]]
+    variants += [("reg", v, 2, r) for v, r in ROW_VARIANTS[(lattice, prec)]]
     if prec != FP64:
         # shared-memory staged kernel: several tiles per row, 2 and 3 stages
         A = 16 // (4 if prec == FP32 else 2)
-        variants += [("staged", A, 2), ("staged", 2 * A, 3)]
-    for vec, form, *st in variants:
+        variants += [("staged", A, 2, 0), ("staged", 2 * A, 3, 0)]
+    for kind, vec, form, rows in variants:
         g = T.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec, **kw)
-        if vec == "staged":
-            g.set_staged(form, st[0])
+        if kind == "staged":
+            g.set_staged(vec, form)
             assert g.variant[0] == 0
         else:
-            g.set_variant(vec, form)
-            assert g.variant[:2] == (vec, form)
+            g.set_variant(vec, form, 0, 0, rows)
+            assert g.variant[:2] == (vec, form) and g.variant[4] == rows
         g.set_populations(f, gg)
         f0, g0 = g.get_populations()  # as stored in the GPU precision
         if ref is None:
@@ -149,10 +156,11 @@ def test_variants_agree_bitwise(T):
     for lattice, shape, prec in ((D2, (301, 45, 1), FP32), (D2, (301, 45, 1), FP16), (D3, (77, 21, 13), FP32),
                                  (D3, (77, 21, 13), BF16)):
         outs = []
-        for vec, form in [v for v in VARIANTS[(lattice, prec)] if v[1] == 2]:
+        trt = [(v, 1) for v, f in VARIANTS[(lattice, prec)] if f == 2] + ROW_VARIANTS[(lattice, prec)]
+        for vec, rows in trt:
             for bx, by in ((128, 1), (64, 2), (32, 4)):
                 g = T.Sim(*shape, lattice=lattice, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
-                g.set_variant(vec, 2, bx, by)
+                g.set_variant(vec, 2, bx, by, rows)
                 g.init(11, 1e-3)
                 g.step(20)
                 outs.append(g.get_populations())
@@ -291,3 +299,39 @@ def test_launch_count(T):
     c0 = g.launches
     g.step(10)
     assert g.launches - c0 == 10
+
+
+def test_graph_replay_matches_plain_launches(T):
+    """Steps replayed from the captured CUDA graph give the same bits as plain
+    launches, for odd and even step counts and after a variant change."""
+    for prec in (FP32, FP16):
+        outs = []
+        for gs in (0, 16, 6):
+            g = T.Sim(131, 67, lattice=D2, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
+            T.tlbm_set_graph(g.h, gs)
+            g.init(3, 1e-3)
+            g.step(5)
+            g.step(37)
+            g.set_variant(2, 2, 0, 0, 1)
+            g.step(20)
+            assert g.launches == 1 + 62 and g.status()[1] == 62
+            outs.append(g.get_populations())
+            g.close()
+        for f, gg in outs[1:]:
+            assert np.array_equal(f, outs[0][0]) and np.array_equal(gg, outs[0][1])
+
+
+def test_side_heated_cavity_is_centro_symmetric(T):
+    """The side-heated cavity of §2.3 (hot left, cold right, adiabatic top and
+    bottom): from the symmetric conductive start the state keeps the cavity's
+    point symmetry, T(x, y) = -T(n-1-x, n-1-y) and u(x, y) = -u(n-1-x, n-1-y)."""
+    n = 65
+    g = T.Sim(n, n, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64, walls=1)
+    g.init(1, 0.0)
+    g.step(6000)
+    m = _fields(g)
+    rot = lambda a: a[::-1, ::-1]
+    assert np.abs(m["T"] + rot(m["T"])).max() < 1e-12
+    assert np.abs(m["ux"] + rot(m["ux"])).max() < 1e-12 and np.abs(m["uy"] + rot(m["uy"])).max() < 1e-12
+    assert np.abs(m["ux"]).max() > 1e-3  # a convective roll has formed
+    assert g.nusselt() > 1.5
