@@ -248,8 +248,8 @@ def tlbm_derived(h) -> list:
     return list(buf[: n.value])
 
 
-def tlbm_set_variant(h, vec=0, form=0, block_x=0, block_y=0):
-    _check(h, lib().tlbm_set_variant(h, int(vec), int(form), int(block_x), int(block_y)))
+def tlbm_set_variant(h, vec=0, form=0, block_x=0, block_y=0, rows=0):
+    _check(h, lib().tlbm_set_variant(h, int(vec), int(form), int(block_x), int(block_y), int(rows)))
 
 
 def tlbm_init_fields(h, T, ux=None, uy=None, uz=None):
@@ -323,7 +323,8 @@ def tlbm_set_staged(h, tile_width=0, stages=0):
 
 
 def tlbm_get_variant(h):
-    v = [C.c_int() for _ in range(4)]
+    """(vec, form, block_x, block_y, rows)"""
+    v = [C.c_int() for _ in range(5)]
     _check(h, lib().tlbm_get_variant(h, *[C.byref(x) for x in v]))
     return tuple(x.value for x in v)
 

@@ -127,3 +127,33 @@ def test_bind_rejects_null_and_small(T):
         assert ei.value.code == T.TLBM_ERR_OOM
     finally:
         T.tlbm_destroy(h)
+
+
+def _declared_arity(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"TLBM_API\s+[\w\s\*]+?\b(tlbm_\w+)\s*\(([^)]*)\)", src):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else len(args.split(","))
+    return out
+
+
+def test_binding_argument_counts_match_the_header(T):
+    """Every ctypes signature has exactly as many arguments as the C declaration,
+    and every Python wrapper passes that many."""
+    import inspect
+
+    arity = _declared_arity("tlbm.h")
+    for name, (res, args) in T._SIGS.items():
+        assert arity[name] == len(args), name
+    for name, n in arity.items():
+        src = inspect.getsource(getattr(T, name)) if hasattr(T, name) else ""
+        call = re.search(r"lib\(\)\." + name + r"\((.*)\)\)", src.replace("\n", " "))
+        if call and "*" not in call.group(1):
+            depth, count = 0, 1
+            for ch in call.group(1):
+                depth += ch in "([{"
+                depth -= ch in ")]}"
+                count += ch == "," and depth == 0
+            assert count == n, (name, count, n)
