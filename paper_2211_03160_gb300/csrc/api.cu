@@ -418,7 +418,7 @@ static VariantDefault default_variant(int dim, int prec) {
     if (dim == 2) {
         switch (prec) {
         case TLBM_FP64: return {2, 64, 1, 1};
-        case TLBM_FP32: return {4, 32, 1, 1};
+        case TLBM_FP32: return {4, 32, 4, 2};
         default: return {4, 32, 4, 1};
         }
     }

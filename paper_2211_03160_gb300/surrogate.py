@@ -179,28 +179,35 @@ def train(net: ConvNet, X: np.ndarray, Y: np.ndarray, iters: int = 2000, lr: flo
     return hist
 
 
-def predict(net: ConvNet, Ra: float, Pr: float):
+def factor(fine: int) -> int:
+    """Fine nodes per coarse interval; the cells are vertex-aligned (fine = 64 k + 1)."""
+    if fine < COARSE or (fine - 1) % (COARSE - 1):
+        raise ValueError(f"fine size {fine} is not 64 k + 1")
+    return (fine - 1) // (COARSE - 1)
+
+
+def predict(net: ConvNet, Ra: float, Pr: float, fine: int = FINE):
     """Coarse (3, 65, 65) FP32 prediction on the device: T, u/U, v/U."""
     import torch
 
     s = torch.cuda.current_stream()
-    x32 = torch.tensor(features(Ra, Pr)[None], dtype=torch.float32, device="cuda")
+    x32 = torch.tensor(features(Ra, Pr, fine=fine)[None], dtype=torch.float32, device="cuda")
     x16 = torch.empty(x32.shape, dtype=torch.bfloat16, device="cuda")
     tlbm.tlbm_to_bf16(x32, x32.numel(), x16, s)
     return net.forward(x16, 1, COARSE, COARSE)[0]
 
 
-def warm_start(h, coarse, U: float):
+def warm_start(h, coarse, U: float, fine: int = FINE):
     """Upsample a coarse (T, u/U, v/U) prediction to the fine cell and start the
     solver from it."""
     import torch
 
     s = torch.cuda.current_stream()
-    fine = torch.empty((3, FINE, FINE), dtype=torch.float32, device="cuda")
-    tlbm.tlbm_upsample_bilinear(coarse.contiguous(), 3, COARSE, COARSE, FACTOR, fine, s)
-    T = fine[0].clamp(-0.5, 0.5).contiguous()
-    ux = (fine[1] * U).contiguous()
-    uy = (fine[2] * U).contiguous()
+    up = torch.empty((3, fine, fine), dtype=torch.float32, device="cuda")
+    tlbm.tlbm_upsample_bilinear(coarse.contiguous(), 3, COARSE, COARSE, factor(fine), up, s)
+    T = up[0].clamp(-0.5, 0.5).contiguous()
+    ux = (up[1] * U).contiguous()
+    uy = (up[2] * U).contiguous()
     tlbm.tlbm_init_fields(h, T, ux, uy, None)
 
 
@@ -211,28 +218,47 @@ def free_fall_steps(n: int = FINE, Ma: float = 0.1) -> int:
     return int(math.ceil(n / (Ma / math.sqrt(3.0))))
 
 
-def generate(draw_list, warm_tf: float, avg_tf: float, samples: int, precision=tlbm.TLBM_FP32):
+def canonical_roll(Y: np.ndarray) -> np.ndarray:
+    """Mirror (x -> 1 - x, u -> -u) every target whose mean circulation is
+    clockwise-negative, so that all targets share one roll direction.
+
+    The sense of the large-scale roll is picked by the initial noise (the cell is
+    mirror-symmetric), so raw time averages of different seeds would cancel in
+    the fit; both senses carry the same Nusselt number."""
+    Y = np.array(Y, copy=True)
+    n = Y.shape[-1]
+    yc = (np.arange(n) - 0.5 * (n - 1))[:, None]
+    for k in range(Y.shape[0]):
+        circ = float((Y[k, 1] * yc).sum())  # u > 0 above the centre, u < 0 below: positive
+        if circ < 0.0:
+            Y[k] = Y[k][:, :, ::-1]
+            Y[k, 1] *= -1.0
+    return Y
+
+
+def generate(draw_list, warm_tf: float, avg_tf: float, samples: int, precision=tlbm.TLBM_FP32, fine: int = FINE):
     """Time-averaged coarse (T, u/U, v/U) of each draw's statistically steady run."""
     import torch
 
-    tf = free_fall_steps()
+    f = factor(fine)
+    tf = free_fall_steps(fine)
     U = 0.1 / math.sqrt(3.0)
-    inst = [(FINE, FINE, 1, Ra, Pr, 0.1, seed) for Ra, Pr, seed in draw_list]
+    inst = [(fine, fine, 1, Ra, Pr, 0.1, seed) for Ra, Pr, seed in draw_list]
     b = tlbm.Batch(inst, lattice=tlbm.TLBM_D2Q9_D2Q5, precision=precision)
     b.init(1e-3)
     b.step(int(warm_tf * tf))
     every = max(1, int(avg_tf * tf / samples))
     acc = torch.zeros((len(inst), 3, COARSE, COARSE), dtype=torch.float64, device="cuda")
-    T = torch.empty((FINE, FINE), dtype=torch.float32, device="cuda")
+    T = torch.empty((fine, fine), dtype=torch.float32, device="cuda")
     ux = torch.empty_like(T)
     uy = torch.empty_like(T)
     for _ in range(samples):
         b.step(every)
         for k in range(len(inst)):
             tlbm.tlbm_batch_macros(b.b, k, None, ux, uy, None, T, tlbm.TLBM_OUT_F32)
-            acc[k, 0] += T[::FACTOR, ::FACTOR]
-            acc[k, 1] += ux[::FACTOR, ::FACTOR] / U
-            acc[k, 2] += uy[::FACTOR, ::FACTOR] / U
+            acc[k, 0] += T[::f, ::f]
+            acc[k, 1] += ux[::f, ::f] / U
+            acc[k, 2] += uy[::f, ::f] / U
     status = b.status()
     b.close()
     return (acc / samples).float().cpu().numpy(), status
@@ -240,7 +266,10 @@ def generate(draw_list, warm_tf: float, avg_tf: float, samples: int, precision=t
 
 def steps_to_steady(nu: np.ndarray, dt: int, window: int, ref: float, tol: float = 0.01, hold: int = 2):
     """First step after which the trailing mean of Nu over `window` samples
-    stays within tol of ref for hold * window samples (None if never)."""
+    stays within tol of ref for hold * window samples (None if never).
+
+    Meaningful for flows that settle to a steady state; a chaotic cell's Nu keeps
+    fluctuating by far more than 1 % and never holds."""
     n = len(nu)
     if n < window:
         return None
@@ -253,19 +282,33 @@ def steps_to_steady(nu: np.ndarray, dt: int, window: int, ref: float, tol: float
     return None
 
 
+def steps_to_reach(nu: np.ndarray, dt: int, window: int, ref: float, tol: float = 0.01):
+    """First step at which the trailing mean of Nu over `window` samples comes
+    within tol of ref or crosses it (None if never): the end of the start-up
+    transient, defined also for a statistically steady, fluctuating Nu."""
+    if len(nu) < window:
+        return None
+    tm = np.convolve(nu, np.ones(window) / window, mode="valid")
+    d = tm - ref
+    for k in range(len(d)):
+        if abs(d[k]) <= tol * abs(ref) or (k > 0 and np.sign(d[k]) != np.sign(d[k - 1])):
+            return (k + window) * dt
+    return None
+
+
 def evaluate(net: ConvNet, draw_list, run_tf: float, ref_tf: float, samples_per_tf: int = 16,
-             precision=tlbm.TLBM_FP32):
+             precision=tlbm.TLBM_FP32, fine: int = FINE):
     """Conductive start vs learned warm start on the same draws (one batch)."""
     import torch
 
-    tf = free_fall_steps()
+    tf = free_fall_steps(fine)
     U = 0.1 / math.sqrt(3.0)
     n = len(draw_list)
-    inst = [(FINE, FINE, 1, Ra, Pr, 0.1, seed) for Ra, Pr, seed in draw_list] * 2
+    inst = [(fine, fine, 1, Ra, Pr, 0.1, seed) for Ra, Pr, seed in draw_list] * 2
     b = tlbm.Batch(inst, lattice=tlbm.TLBM_D2Q9_D2Q5, precision=precision)
     b.init(1e-3)
     for k, (Ra, Pr, _) in enumerate(draw_list):
-        warm_start(b.instance(n + k), predict(net, Ra, Pr), U)
+        warm_start(b.instance(n + k), predict(net, Ra, Pr, fine), U, fine)
     torch.cuda.synchronize()
     dt = max(1, tf // samples_per_tf)
     total = int(run_tf * samples_per_tf)
@@ -281,11 +324,27 @@ def evaluate(net: ConvNet, draw_list, run_tf: float, ref_tf: float, samples_per_
     ref_samples = int(ref_tf * samples_per_tf)
     for k, (Ra, Pr, seed) in enumerate(draw_list):
         ref = float(nus[k, -ref_samples:].mean())
-        cold = steps_to_steady(nus[k], dt, window, ref)
-        warm = steps_to_steady(nus[n + k], dt, window, ref)
-        out.append({"Ra": Ra, "Pr": Pr, "Nu_ref": ref, "steps_conductive": cold, "steps_warm": warm,
+        tail = nus[k, -ref_samples:]
+        out.append({"Ra": Ra, "Pr": Pr, "Nu_ref": ref, "Nu_ref_rel_std": float(tail.std() / abs(ref)),
+                    "steps_conductive": steps_to_reach(nus[k], dt, window, ref),
+                    "steps_warm": steps_to_reach(nus[n + k], dt, window, ref),
+                    "held_conductive": steps_to_steady(nus[k], dt, window, ref),
+                    "held_warm": steps_to_steady(nus[n + k], dt, window, ref),
                     "diverged": bool(status[k] or status[n + k])})
     return out, series
+
+
+def summarize(ev) -> dict:
+    """Median step ratio conductive / warm for both criteria, over the draws
+    where both runs met it."""
+    res = {}
+    for key, a, b in (("reach", "steps_conductive", "steps_warm"), ("held", "held_conductive", "held_warm")):
+        both = [e for e in ev if e[a] and e[b] and not e["diverged"]]
+        res[key] = {"compared": len(both), "warm_faster": sum(e[b] < e[a] for e in both),
+                    "median_speedup": float(np.median([e[a] / e[b] for e in both])) if both else None,
+                    "median_steps_conductive": float(np.median([e[a] for e in both])) if both else None,
+                    "median_steps_warm": float(np.median([e[b] for e in both])) if both else None}
+    return res
 
 
 def main(argv=None):
@@ -300,41 +359,41 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=3000)
     ap.add_argument("--run-tf", type=float, default=60.0)
     ap.add_argument("--ref-tf", type=float, default=20.0)
+    ap.add_argument("--fine", type=int, default=FINE, help="fine cell size, 64 k + 1")
+    ap.add_argument("--log-ra", type=float, nargs=2, default=(6.0, 8.0), help="log10 Ra range of the draws")
     ap.add_argument("--out", default="")
     ap.add_argument("--save-data", default="", help="write the generated training targets (.npz)")
     ap.add_argument("--load-data", default="", help="reuse training targets written by --save-data")
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
     t0 = time.time()
-    tr = draws(args.train_draws, seed=1)
+    tr = draws(args.train_draws, seed=1, log_ra=tuple(args.log_ra))
     if args.load_data:
         z = np.load(args.load_data)
         Y, st = z["Y"], list(z["status"])
     else:
-        Y, st = generate(tr, args.warm_tf, args.avg_tf, args.samples)
+        Y, st = generate(tr, args.warm_tf, args.avg_tf, args.samples, fine=args.fine)
     if args.save_data:
         np.savez(args.save_data, Y=Y, status=np.array(st))
-    X = np.stack([features(Ra, Pr) for Ra, Pr, _ in tr])
+    Y = canonical_roll(Y)
+    X = np.stack([features(Ra, Pr, fine=args.fine) for Ra, Pr, _ in tr])
     keep = [k for k in range(len(tr)) if not st[k] and np.isfinite(Y[k]).all()]
     t1 = time.time()
     net = ConvNet(seed=0)
     hist = train(net, X[keep], Y[keep], iters=args.iters)
     torch.cuda.synchronize()
     t2 = time.time()
-    ev, series = evaluate(net, draws(args.eval_draws, seed=2), args.run_tf, args.ref_tf)
+    ev, series = evaluate(net, draws(args.eval_draws, seed=2, log_ra=tuple(args.log_ra)), args.run_tf, args.ref_tf,
+                          fine=args.fine)
     t3 = time.time()
-    res = {"train_draws": len(tr), "train_kept": len(keep), "loss": hist, "eval": ev, "series": series,
+    res = {"fine": args.fine, "log_ra": list(args.log_ra), "train_draws": len(tr), "train_kept": len(keep),
+           "loss": hist, "summary": summarize(ev), "eval": ev, "series": series,
            "seconds": {"data": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}
-    both = [e for e in ev if e["steps_conductive"] and e["steps_warm"] and not e["diverged"]]
-    if both:
-        res["median_speedup"] = float(np.median([e["steps_conductive"] / e["steps_warm"] for e in both]))
-        res["warm_faster"] = sum(e["steps_warm"] < e["steps_conductive"] for e in both)
-        res["compared"] = len(both)
-    txt = json.dumps(res)
     if args.out:
         with open(args.out, "w") as fh:
-            fh.write(txt)
-    print(txt)
+            fh.write(json.dumps(res))
+    del res["series"]
+    print(json.dumps(res))
     return 0
 
 
