@@ -44,7 +44,8 @@ BYTES_PER_LU = {(2, "fp64"): 224, (2, "fp32"): 112, (2, "fp16"): 56, (2, "bf16")
 KERNEL_SOURCES = ["paper_2211_03160_gb300/csrc/kernels.cuh", "paper_2211_03160_gb300/csrc/lattice.cuh",
                   "paper_2211_03160_gb300/csrc/dispatch.h", "paper_2211_03160_gb300/csrc/step_2d_f32.cu",
                   "paper_2211_03160_gb300/csrc/step_2d_f16.cu", "paper_2211_03160_gb300/csrc/step_3d_f32.cu",
-                  "paper_2211_03160_gb300/csrc/step_3d_f16.cu", "paper_2211_03160_gb300/csrc/step_fp64.cu"]
+                  "paper_2211_03160_gb300/csrc/step_3d_f16.cu", "paper_2211_03160_gb300/csrc/step_fp64.cu",
+                  "paper_2211_03160_gb300/csrc/staged.cuh", "paper_2211_03160_gb300/csrc/step_staged.cu"]
 
 
 def kernel_hash() -> str:

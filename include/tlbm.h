@@ -206,12 +206,16 @@ TLBM_API int tlbm_derived(tlbm_t h, double* out, int cap, int* count);
  * TLBM_ERR_UNSUPPORTED if the variant is not compiled. */
 TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y, int rows);
 /* Use the shared-memory staged step kernel instead: a persistent grid whose
- * blocks copy each tile's source rows (one row segment of tile_width nodes per
- * population) into shared memory with TMA bulk copies completing on mbarriers,
- * `stages` tiles in flight per block (0 = defaults: whole rows in 3D, 512 nodes in
- * 2D; 4 stages).  FP32/FP16/BF16 storage with two-relaxation-time rates only
- * (TLBM_ERR_UNSUPPORTED otherwise).  A block that waits too long for its copies
- * gives up; the next synchronising call then returns TLBM_ERR_TIMEOUT.
+ * blocks move each tile (one row segment of tile_width nodes) with TMA bulk
+ * copies: one warp copies the tile's source row of every population into
+ * shared memory (completing on mbarriers), 4 or 8 warps collide two nodes per
+ * thread and write the results back in place, and the tile leaves with bulk
+ * copies shared -> global; `stages` tiles are in flight per block.
+ * tile_width: a multiple of 16 bytes' worth of elements, at most 512 (0 =
+ * whole rows up to 512 nodes, else 512); stages: 3 .. 8 (0 = the most that leave
+ * two blocks per SM).  FP32/FP16/BF16 storage with two-relaxation-time rates
+ * only (TLBM_ERR_UNSUPPORTED otherwise).  A block that waits too long for its
+ * copies gives up; the next synchronising call then returns TLBM_ERR_TIMEOUT.
  * tlbm_set_variant switches back to the register kernels. */
 TLBM_API int tlbm_set_staged(tlbm_t h, int tile_width, int stages);
 /* Current variant (form reported as 1 MRT or 2 TRT; vec 0 for the staged

@@ -47,6 +47,7 @@ static int cuda_fail(tlbm_t h, cudaError_t e, const char* what) {
 }
 
 static void drop_graph(tlbm_t h);
+static int set_staged(tlbm_t h, int tile_width, int stages);
 
 #define TLBM_CHECK_HANDLE(h)                                   \
     do {                                                       \
@@ -419,13 +420,13 @@ static VariantDefault default_variant(int dim, int prec) {
         switch (prec) {
         case TLBM_FP64: return {2, 64, 1, 1};
         case TLBM_FP32: return {4, 32, 4, 2};
-        default: return {4, 32, 4, 1};
+        default: return {4, 32, 1, 1};
         }
     }
     switch (prec) {
     case TLBM_FP64: return {1, 32, 4, 1};
     case TLBM_FP32: return {1, 32, 2, 1};
-    default: return {1, 32, 8, 1};
+    default: return {2, 32, 1, 1};
     }
 }
 static int default_vec(int dim, int prec) { return default_variant(dim, prec).vec; }
@@ -638,6 +639,14 @@ extern "C" int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes) {
     h->buf[0] = h->mem;
     h->buf[1] = h->mem + h->popset_bytes;
     h->cur = 0;
+    // 2D FP16/BF16 storage with two-relaxation-time rates defaults to the
+    // shared-memory staged kernel (512-node tiles, 3 stages: the fastest on
+    // GB300); the register kernel stays if the device cannot host it
+    if (!h->variant_chosen && h->dim == 2 && (h->prec == TLBM_FP16_OFFSET || h->prec == TLBM_BF16_OFFSET) &&
+        h->kp.trt && set_staged(h, 512, 3) != TLBM_OK) {
+        h->staged = 0;
+        h->err[0] = 0;
+    }
     return TLBM_OK;
 }
 
@@ -687,15 +696,13 @@ static cudaError_t launch_step_raw(tlbm_t h, int parity, cudaStream_t s) {
     const void* src = h->buf[parity];
     void* dst = h->buf[parity ^ 1];
     if (h->staged) {
-        const int A = 16 / (int)h->elem;
         StagedInfo si;
         si.tw = h->staged_tw;
         si.tiles_per_row = (h->nx + si.tw - 1) / si.tw;
-        si.tiles = (long long)h->ny * h->nz * si.tiles_per_row;
-        si.lw = si.tw + 2 * A;
+        si.tiles = h->ny * h->nz * si.tiles_per_row;
         si.stages = h->staged_stages;
         si.status = (int*)(h->mem + h->status_off);
-        return launch_staged(h->dim, h->prec, src, dst, kp, si, h->staged_grid, h->staged_smem, s);
+        return launch_staged(h->dim, h->prec, h->staged_nc, src, dst, kp, si, h->staged_grid, h->staged_smem, s);
     }
     const int vec = h->vec;
     const int bx = h->bx, by = h->by, rows = h->rows;
@@ -951,46 +958,78 @@ extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bl
     h->by = by;
     h->rows = nr;
     h->staged = 0;
+    h->variant_chosen = 1;
     h->kp.xmax_load = h->kp.L.P - v;
+    drop_graph(h);
+    return TLBM_OK;
+}
+
+static int set_staged(tlbm_t h, int tile_width, int stages) {
+    if (h->prec == TLBM_FP64) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel has no FP64 variant");
+    if (!h->kp.trt) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel needs two-relaxation-time rates");
+    const int A = 16 / (int)h->elem;
+    const int nx_a = (h->nx + A - 1) / A * A;
+    // default: whole rows up to 512 nodes, else 512-node segments
+    int tw = tile_width > 0 ? tile_width : std::min(512, nx_a);
+    if (tw % A || tw < A || tw > 512)
+        return fail(h, TLBM_ERR_ARG, "tile_width must be a multiple of %d in [%d, 512]", A, A);
+    if (tw > nx_a) tw = nx_a;
+    const int nc = tw > 256 ? 8 : 4;  // consumer warps: one pair of nodes per thread
+    const int lw = 64 * nc + 2 * A;   // shared row length per population (elements)
+    const size_t stage_bytes = (size_t)(h->qf + h->qg) * lw * h->elem;
+    const void* fn = staged_function(h->dim, h->prec, nc);
+    if (!fn) return fail(h, TLBM_ERR_UNSUPPORTED, "staged kernel not built for this precision");
+    int dev = 0, optin = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
+    // allow the device's full opt-in shared memory for this kernel, so that
+    // handles with different tile shapes can share it
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute (shared memory size)");
+    const int threads = 32 * (nc + 1);
+    int ns = stages;
+    if (ns <= 0) {
+        // the most stages that still leave two blocks per SM, else the most for one
+        ns = 0;
+        for (int want = 2; want >= 1 && ns == 0; --want)
+            for (int k = TILE_MAX_STAGES; k >= 2; --k) {
+                int b = 0;
+                const size_t sm = 512 + (size_t)k * stage_bytes;
+                if (sm > (size_t)optin) continue;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, sm);
+                if (e != cudaSuccess) return cuda_fail(h, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+                if (b >= want) {
+                    ns = k;
+                    break;
+                }
+            }
+        if (ns == 0) return fail(h, TLBM_ERR_ARG, "two stages of %zu bytes do not fit in shared memory", stage_bytes);
+    }
+    if (ns < 2 || ns > TILE_MAX_STAGES) return fail(h, TLBM_ERR_ARG, "stages must be in [2, %d]", TILE_MAX_STAGES);
+    const size_t smem = 512 + (size_t)ns * stage_bytes;
+    if (smem > (size_t)optin) return fail(h, TLBM_ERR_ARG, "%zu bytes of shared memory per block exceed %d", smem, optin);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(h, TLBM_ERR_ARG, "%zu bytes of shared memory per block do not fit", smem);
+    const long long tiles = (long long)h->ny * h->nz * ((h->nx + tw - 1) / tw);
+    if (tiles >= (1ll << 31)) return fail(h, TLBM_ERR_ARG, "too many tiles for the staged kernel");
+    h->staged = 1;
+    h->staged_tw = tw;
+    h->staged_nc = nc;
+    h->staged_stages = ns;
+    h->staged_smem = smem;
+    h->staged_grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
     drop_graph(h);
     return TLBM_OK;
 }
 
 extern "C" int tlbm_set_staged(tlbm_t h, int tile_width, int stages) {
     TLBM_CHECK_HANDLE(h);
-    if (h->prec == TLBM_FP64) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel has no FP64 variant");
-    if (!h->kp.trt) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel needs two-relaxation-time rates");
-    const int A = 16 / (int)h->elem;
-    int tw = tile_width > 0 ? tile_width : (h->dim == 3 ? (h->nx + A - 1) / A * A : 512);
-    if (tw % A || tw < A || tw > 4096)
-        return fail(h, TLBM_ERR_ARG, "tile_width must be a multiple of %d in [%d, 4096]", A, A);
-    const int ns = stages > 0 ? stages : 4;
-    if (ns < 2 || ns > STAGED_MAX_STAGES) return fail(h, TLBM_ERR_ARG, "stages must be in [2, %d]", STAGED_MAX_STAGES);
-    const size_t smem = 128 + (size_t)ns * (h->qf + h->qg) * (size_t)(tw + 2 * A) * h->elem;
-    const void* fn = staged_function(h->dim, h->prec);
-    if (!fn) return fail(h, TLBM_ERR_UNSUPPORTED, "staged kernel not built for this precision");
-    // allow the device's full opt-in shared memory for this kernel, so that
-    // handles with different tile shapes can share it
-    int dev = 0, optin = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
-    if (smem > (size_t)optin) return fail(h, TLBM_ERR_ARG, "%zu bytes of shared memory per block exceed %d", smem, optin);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute (shared memory size)");
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, STAGED_THREADS, smem);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm < 1) return fail(h, TLBM_ERR_ARG, "%zu bytes of shared memory per block do not fit", smem);
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
-    const long long tiles = (long long)h->ny * h->nz * ((h->nx + tw - 1) / tw);
-    h->staged = 1;
-    h->staged_tw = tw;
-    h->staged_stages = ns;
-    h->staged_smem = smem;
-    h->staged_grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
-    drop_graph(h);
-    return TLBM_OK;
+    const int rc = set_staged(h, tile_width, stages);
+    if (rc == TLBM_OK) h->variant_chosen = 1;
+    return rc;
 }
 
 extern "C" int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y, int* rows) {

@@ -19,10 +19,11 @@ bool step_variant_available(int dim, int prec, int vec, bool trt, int rows);
 // device function of a compiled variant (for cudaFuncGetAttributes), or nullptr
 const void* step_function(int dim, int prec, int vec, bool trt, int rows);
 
-// shared-memory staged (TMA bulk copy) step, TRT form, FP32/FP16/BF16 storage
-const void* staged_function(int dim, int prec);
-cudaError_t launch_staged(int dim, int prec, const void* src, void* dst, const KParams& p, const StagedInfo& si,
-                          int grid, size_t smem, cudaStream_t s);
+// shared-memory staged (TMA bulk copy) step, TRT form, FP32/FP16/BF16 storage,
+// nc = 4 or 8 consumer warps
+const void* staged_function(int dim, int prec, int nc);
+cudaError_t launch_staged(int dim, int prec, int nc, const void* src, void* dst, const KParams& p,
+                          const StagedInfo& si, int grid, size_t smem, cudaStream_t s);
 
 // per-unit entry points
 cudaError_t launch_step_2d_f32(int vec, bool trt, int rows, const void*, void*, const KParams&, dim3, dim3,

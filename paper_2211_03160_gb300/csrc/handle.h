@@ -20,7 +20,8 @@ struct tlbm_s {
     cudaGraphExec_t graph;     // captured block of graph_steps steps starting from buffer 0
     cudaStream_t capture_stream;
     int staged;                // 1: shared-memory staged (TMA bulk copy) kernel
-    int staged_tw, staged_stages, staged_grid;
+    int variant_chosen;        // set by tlbm_set_variant / tlbm_set_staged: keep the caller's choice
+    int staged_tw, staged_nc, staged_stages, staged_grid;
     size_t staged_smem;
     size_t elem;               // bytes per stored value
     size_t popset_bytes;       // one population buffer (f planes then g planes)

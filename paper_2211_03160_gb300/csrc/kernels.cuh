@@ -402,11 +402,188 @@ __device__ __forceinline__ void collide_trt(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<D
     });
 }
 
+// ------------------------------------------------------------------ FP32 pairs
+//
+// sm_100-class SMs execute two independent FP32 operations per instruction on a
+// register pair (FADD2 / FMUL2 / FFMA2; each half is an ordinary IEEE
+// round-to-nearest operation).  The FP32 two-relaxation-time collision is
+// therefore written once over V = float (one node) and V = float2 (two
+// x-adjacent nodes of one thread), with explicit, never-contracted operations,
+// so that a node gets bitwise the same result whichever form updates it.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+template <class V> __device__ __forceinline__ V vbc(float x);
+template <> __device__ __forceinline__ float vbc<float>(float x) { return x; }
+template <> __device__ __forceinline__ float2 vbc<float2>(float x) { return make_float2(x, x); }
+// a - b as one rounding (b * -1 is exact)
+template <class V> __device__ __forceinline__ V vsub(V a, V b) { return vfma(b, vbc<V>(-1.0f), a); }
+
+// Sum over the velocity components with coefficients c in {-1, 0, 1}; the first
+// non-zero coefficient must be +1.
+template <class V, int CX, int CY, int CZ>
+__device__ __forceinline__ V vdot_unit(V x, V y, V z) {
+    static_assert(CX == 1 || (CX == 0 && CY == 1) || (CX == 0 && CY == 0 && CZ == 1), "first coefficient +1");
+    V r = CX ? x : (CY ? y : z);
+    if constexpr (CX != 0 && CY == 1) r = vadd(r, y);
+    if constexpr (CX != 0 && CY == -1) r = vsub(r, y);
+    if constexpr ((CX != 0 || CY != 0) && CZ == 1) r = vadd(r, z);
+    if constexpr ((CX != 0 || CY != 0) && CZ == -1) r = vsub(r, z);
+    return r;
+}
+
+// The collision of collide_trt above in FP32, over V = float or float2.  Per
+// pair (i, ibar) the direction with a leading +1 component, e*, carries the
+// antisymmetric part: with sg = +1 if e_i = e*, -1 otherwise,
+//   d_i+ = c1 d_i + c2 d_ibar + Ks + sg Ka*,  d_ibar+ = c1 d_ibar + c2 d_i + Ks - sg Ka*,
+//   Ks  = ws K0 + e*.u (R1w e*.u + R2w e*.F),   Ka* = R3w e*.u + R4w e*.F,
+// where R1w = 4.5 sp rho ws, R2w = 9 (1 - sp/2) ws, R3w = 3 sm rho ws,
+// R4w = 3 (1 - sm/2) ws and ws = w_i * scale (the same terms as above, with
+// the lattice weight folded in per weight class).
+template <int DIM, class V, bool SCALED>
+__device__ __forceinline__ void collide_trt_v(V (&d)[Lat<DIM>::F::Q], V (&g)[Lat<DIM>::G::Q], const KParams& p) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    using P = PV<float>;
+    const V zero = vbc<V>(0.0f);
+    V drs = d[0], jx = zero, jy = zero, jz = zero;
+    static_for<LF::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        if constexpr (i > 0) drs = vadd(drs, d[i]);
+        if constexpr (LF::e(i, 0) == 1) jx = vadd(jx, d[i]);
+        if constexpr (LF::e(i, 0) == -1) jx = vsub(jx, d[i]);
+        if constexpr (LF::e(i, 1) == 1) jy = vadd(jy, d[i]);
+        if constexpr (LF::e(i, 1) == -1) jy = vsub(jy, d[i]);
+        if constexpr (LF::e(i, 2) == 1) jz = vadd(jz, d[i]);
+        if constexpr (LF::e(i, 2) == -1) jz = vsub(jz, d[i]);
+    });
+    V Ts = g[0];
+    static_for<LG::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        if constexpr (i > 0) Ts = vadd(Ts, g[i]);
+    });
+    const float sc = SCALED ? ScaleOf<float>::s(p) : 1.0f;
+    const V inv = vbc<V>(SCALED ? ScaleOf<float>::inv(p) : 1.0f);
+    const V drho = SCALED ? vmul(drs, inv) : drs;
+    const V T = SCALED ? vmul(Ts, inv) : Ts;
+    const V rho = vadd(vbc<V>(1.0f), drho);
+    const V buoy = vmul(vbc<V>(P::gbeta(p)), T);
+    const V Fx = vmul(rho, vbc<V>(P::body(p, 0)));
+    const V Fy = vmul(rho, DIM == 2 ? vadd(buoy, vbc<V>(P::body(p, 1))) : vbc<V>(P::body(p, 1)));
+    const V Fz = DIM == 3 ? vmul(rho, vadd(buoy, vbc<V>(P::body(p, 2)))) : zero;
+    const V ir = vrcp(rho);
+    const V half = vbc<V>(0.5f);
+    const V ux = vmul(vfma(jx, inv, vmul(half, Fx)), ir);
+    const V uy = vmul(vfma(jy, inv, vmul(half, Fy)), ir);
+    const V uz = DIM == 3 ? vmul(vfma(jz, inv, vmul(half, Fz)), ir) : zero;
+    const float sp = P::sp(p), sm = P::sm(p), shp = P::shp(p), shm = P::shm(p);
+    const V uu = DIM == 3 ? vfma(ux, ux, vfma(uy, uy, vmul(uz, uz))) : vfma(ux, ux, vmul(uy, uy));
+    const V uF = DIM == 3 ? vfma(ux, Fx, vfma(uy, Fy, vmul(uz, Fz))) : vfma(ux, Fx, vmul(uy, Fy));
+    // K0 = sp (drho - 1.5 rho u^2) - 3 (1 - sp/2) u.F
+    const V K0 = vfma(vbc<V>(sp), vfma(rho, vmul(vbc<V>(-1.5f), uu), drho), vmul(vbc<V>(-3.0f * shp), uF));
+    const V R1 = vmul(vbc<V>(4.5f * sp), rho), R3 = vmul(vbc<V>(3.0f * sm), rho);
+    const float c1 = 1.0f - 0.5f * (sp + sm), c2 = 0.5f * (sm - sp);
+    {
+        constexpr float w0 = weight<LF, float>(0);
+        d[0] = vfma(vbc<V>(1.0f - sp), d[0], vmul(vbc<V>(w0 * sc), K0));
+    }
+    // per weight class (D2Q9: 1/9, 1/36; D3Q19: 1/18, 1/36)
+    constexpr float wa = weight<LF, float>(1), wb = weight<LF, float>(LF::Q - 1);
+    const V wKa = vmul(vbc<V>(wa * sc), K0), wKb = vmul(vbc<V>(wb * sc), K0);
+    const V R1a = vmul(vbc<V>(wa * sc), R1), R1b = vmul(vbc<V>(wb * sc), R1);
+    const V R3a = vmul(vbc<V>(wa * sc), R3), R3b = vmul(vbc<V>(wb * sc), R3);
+    static_for<LF::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        constexpr int o = LF::opp(i);
+        if constexpr (i != 0 && i < o) {
+            constexpr int ex = LF::e(i, 0), ey = LF::e(i, 1), ez = LF::e(i, 2);
+            constexpr int sg = ex != 0 ? ex : (ey != 0 ? ey : ez);
+            constexpr bool cls_a = LF::w36(i) == LF::w36(1);
+            static_assert(cls_a || LF::w36(i) == LF::w36(LF::Q - 1), "two weight classes");
+            const float ws = (cls_a ? wa : wb) * sc;
+            const V eu = vdot_unit<V, sg * ex, sg * ey, sg * ez>(ux, uy, uz);
+            const V eF = vdot_unit<V, sg * ex, sg * ey, sg * ez>(Fx, Fy, Fz);
+            const V Ks = vfma(eu, vfma(cls_a ? R1a : R1b, eu, vmul(vbc<V>(9.0f * shp * ws), eF)), cls_a ? wKa : wKb);
+            const V Ka = vfma(cls_a ? R3a : R3b, eu, vmul(vbc<V>(3.0f * shm * ws), eF));
+            const V sum = sg > 0 ? vadd(Ks, Ka) : vsub(Ks, Ka);
+            const V dif = sg > 0 ? vsub(Ks, Ka) : vadd(Ks, Ka);
+            const V di = d[i], dob = d[o];
+            d[i] = vfma(vbc<V>(c1), di, vfma(vbc<V>(c2), dob, sum));
+            d[o] = vfma(vbc<V>(c1), dob, vfma(vbc<V>(c2), di, dif));
+        }
+    });
+    // thermal
+    const float qp = P::qp(p), qm = P::qm(p);
+    const float wT = 0.5f * P::omega(p);
+    const float t1 = 1.0f - 0.5f * (qp + qm), t2 = 0.5f * (qm - qp);
+    const V Ks_T = vmul(vbc<V>(qp * wT), Ts);   // scaled like g
+    const V ka_T = vmul(vbc<V>(0.5f * qm), Ts); // times e.u
+    g[0] = vfma(vbc<V>(1.0f - qp), g[0], vmul(vbc<V>(qp * (1.0f - float(LG::Q - 1) * wT)), Ts));
+    static_for<LG::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        constexpr int o = LG::opp(i);
+        if constexpr (i != 0 && i < o) {
+            constexpr int ex = LG::e(i, 0), ey = LG::e(i, 1), ez = LG::e(i, 2);
+            constexpr int sg = ex != 0 ? ex : (ey != 0 ? ey : ez);
+            const V eu = ex != 0 ? ux : (ey != 0 ? uy : uz);
+            const V Ka = vmul(ka_T, eu);
+            const V sum = sg > 0 ? vadd(Ks_T, Ka) : vsub(Ks_T, Ka);
+            const V dif = sg > 0 ? vsub(Ks_T, Ka) : vadd(Ks_T, Ka);
+            const V gi = g[i], go = g[o];
+            g[i] = vfma(vbc<V>(t1), gi, vfma(vbc<V>(t2), go, sum));
+            g[o] = vfma(vbc<V>(t1), go, vfma(vbc<V>(t2), gi, dif));
+        }
+    });
+}
+
 template <int DIM, bool TRT, class C, bool SCALED = false>
 __device__ __forceinline__ void collide(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q], const KParams& p) {
-    if constexpr (TRT) collide_trt<DIM, C, SCALED>(d, g, p);
+    if constexpr (TRT && std::is_same<C, float>::value) collide_trt_v<DIM, float, SCALED>(d, g, p);
+    else if constexpr (TRT) collide_trt<DIM, C, SCALED>(d, g, p);
     else if constexpr (DIM == 2) collide_2d<C>(d, g, p);
     else collide_3d<C>(d, g, p);
+}
+
+// Collide the nodes k = 0 .. VEC-1 of f[i][k], g[i][k]; two at a time on the
+// FP32 pair instructions where the form and the count allow.
+template <int DIM, bool TRT, class C, bool KS, int VEC>
+__device__ __forceinline__ void collide_vec(C (&f)[Lat<DIM>::F::Q][VEC], C (&g)[Lat<DIM>::G::Q][VEC],
+                                            const KParams& p) {
+    constexpr int QF = Lat<DIM>::F::Q, QG = Lat<DIM>::G::Q;
+    if constexpr (TRT && std::is_same<C, float>::value && VEC % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC; k += 2) {
+            float2 fd[QF], gd[QG];
+#pragma unroll
+            for (int i = 0; i < QF; ++i) fd[i] = make_float2(f[i][k], f[i][k + 1]);
+#pragma unroll
+            for (int i = 0; i < QG; ++i) gd[i] = make_float2(g[i][k], g[i][k + 1]);
+            collide_trt_v<DIM, float2, KS>(fd, gd, p);
+#pragma unroll
+            for (int i = 0; i < QF; ++i) { f[i][k] = fd[i].x; f[i][k + 1] = fd[i].y; }
+#pragma unroll
+            for (int i = 0; i < QG; ++i) { g[i][k] = gd[i].x; g[i][k + 1] = gd[i].y; }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            C fd[QF], gd[QG];
+#pragma unroll
+            for (int i = 0; i < QF; ++i) fd[i] = f[i][k];
+#pragma unroll
+            for (int i = 0; i < QG; ++i) gd[i] = g[i][k];
+            collide<DIM, TRT, C, KS>(fd, gd, p);
+#pragma unroll
+            for (int i = 0; i < QF; ++i) f[i][k] = fd[i];
+#pragma unroll
+            for (int i = 0; i < QG; ++i) g[i][k] = gd[i];
+        }
+    }
 }
 
 // Node macros from deviations (used by the diagnostic kernels).
@@ -646,6 +823,64 @@ __device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, 
     }
 }
 
+// The populations with e_x = SIDE of node k of a thread's VEC nodes, for a node
+// on the x face SIDE of an inner row (y, z away from the faces) with x not
+// periodic: those, and only those, leave the cell, through that face.
+template <class LS, bool THERMAL, int SIDE, class S, int VEC, class C, bool KS>
+__device__ __forceinline__ void x_face(S* __restrict__ base, const KParams& p, int x, int y, int z, int k,
+                                       const C (&v)[LS::Q][VEC]) {
+    const C scale = ScaleOf<C>::s(p);
+    const C un = KS ? ScaleOf<C>::inv(p) : C(1);  // the wall rules take unscaled values
+    static_for<LS::Q>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        if constexpr (LS::e(i, 0) == SIDE) {
+            C val = v[i][0];
+#pragma unroll
+            for (int kk = 1; kk < VEC; ++kk)
+                if (k == kk) val = v[i][kk];
+            ghost_write<LS, THERMAL, i, S, C>(base, p, x, y, z, KS ? val * un : val, scale);
+        }
+    });
+}
+
+// Wall and periodic rules for the post-collision values of a thread's nodes.
+// Threads holding x = 0 or x = nx - 1 of an inner row only have the x-face
+// populations to place (inline); rows on a y or z face, and periodic x, take the
+// general out-of-line path.
+template <int DIM, class S, int VEC, class C, bool KS>
+__device__ __forceinline__ void wall_writes(S* __restrict__ dst, const KParams& p, int x0, int y, int z,
+                                            const C (&f)[Lat<DIM>::F::Q][VEC], const C (&g)[Lat<DIM>::G::Q][VEC]) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    constexpr int QF = LF::Q, QG = LG::Q;
+    const Layout& L = p.L;
+    const bool xlo = x0 == 0, xhi = x0 + VEC >= L.nx;
+    const bool face_row = (y == 0) || (y == L.ny - 1) || (DIM == 3 && (z == 0 || z == L.nz - 1));
+    if (face_row || ((xlo || xhi) && (p.periodic & 1))) {
+        C post[(QF + QG) * VEC];
+        const C un = KS ? ScaleOf<C>::inv(p) : C(1);  // the wall rules take unscaled values
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+#pragma unroll
+            for (int i = 0; i < QF; ++i) post[i * VEC + k] = KS ? f[i][k] * un : f[i][k];
+#pragma unroll
+            for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = KS ? g[i][k] * un : g[i][k];
+        }
+        edge_writes<DIM, S, VEC, C>(dst, p, x0, y, z, post);
+        return;
+    }
+    S* __restrict__ gdst = dst + (long long)QF * L.plane;
+    if (xlo) {
+        x_face<LF, false, -1, S, VEC, C, KS>(dst, p, 0, y, z, 0, f);
+        x_face<LG, true, -1, S, VEC, C, KS>(gdst, p, 0, y, z, 0, g);
+    }
+    if (xhi) {
+        const int k = L.nx - 1 - x0;
+        x_face<LF, false, 1, S, VEC, C, KS>(dst, p, L.nx - 1, y, z, k, f);
+        x_face<LG, true, 1, S, VEC, C, KS>(gdst, p, L.nx - 1, y, z, k, g);
+    }
+}
+
 // One thread updates VEC consecutive nodes of one row.  blockDim.x must be a
 // multiple of 32 so that a warp covers 32*VEC consecutive nodes of one row.
 // Body of the step for the block at grid position (bx, by, bz) of one cell.
@@ -671,19 +906,7 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
     C f[QF][VEC], g[QG][VEC];
     pull_node_vec<DIM, S, VEC, C, KS>(src + row + x0ld, p, lane, f, g);
 
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-        C fd[QF], gd[QG];
-#pragma unroll
-        for (int i = 0; i < QF; ++i) fd[i] = f[i][k];
-#pragma unroll
-        for (int i = 0; i < QG; ++i) gd[i] = g[i][k];
-        collide<DIM, TRT, C, KS>(fd, gd, p);
-#pragma unroll
-        for (int i = 0; i < QF; ++i) f[i][k] = fd[i];
-#pragma unroll
-        for (int i = 0; i < QG; ++i) g[i][k] = gd[i];
-    }
+    collide_vec<DIM, TRT, C, KS, VEC>(f, g, p);
 
     if (x0 >= L.nx) return;
     S* __restrict__ own = dst + row + x0;
@@ -719,20 +942,7 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
     }
 
     // wall and periodic rules for values that leave the cell
-    const bool edge = (x0 == 0) || (x0 + VEC >= L.nx) || (y == 0) || (y == L.ny - 1) ||
-                      (DIM == 3 && (z == 0 || z == L.nz - 1));
-    if (edge) {
-        C post[(QF + QG) * VEC];
-        const C un = KS ? ScaleOf<C>::inv(p) : C(1);  // the wall rules take unscaled values
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-#pragma unroll
-            for (int i = 0; i < QF; ++i) post[i * VEC + k] = KS ? f[i][k] * un : f[i][k];
-#pragma unroll
-            for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = KS ? g[i][k] * un : g[i][k];
-        }
-        edge_writes<DIM, S, VEC, C>(dst, p, x0, y, z, post);
-    }
+    wall_writes<DIM, S, VEC, C, KS>(dst, p, x0, y, z, f, g);
 }
 
 // ------------------------------------------------------------------ software-pipelined rows
@@ -815,19 +1025,7 @@ __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p
     constexpr int QF = LF::Q, QG = LG::Q;
     const Layout& L = p.L;
     const C scale = ScaleOf<C>::s(p);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-        C fd[QF], gd[QG];
-#pragma unroll
-        for (int i = 0; i < QF; ++i) fd[i] = f[i][k];
-#pragma unroll
-        for (int i = 0; i < QG; ++i) gd[i] = g[i][k];
-        collide<DIM, TRT, C, KS>(fd, gd, p);
-#pragma unroll
-        for (int i = 0; i < QF; ++i) f[i][k] = fd[i];
-#pragma unroll
-        for (int i = 0; i < QG; ++i) g[i][k] = gd[i];
-    }
+    collide_vec<DIM, TRT, C, KS, VEC>(f, g, p);
     if (x0 >= L.nx) return;
     S* __restrict__ own = dst + row + x0;
     if (x0 + VEC <= L.nx) {
@@ -860,20 +1058,7 @@ __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p
             }
         }
     }
-    const bool edge = (x0 == 0) || (x0 + VEC >= L.nx) || (y == 0) || (y == L.ny - 1) ||
-                      (DIM == 3 && (z == 0 || z == L.nz - 1));
-    if (edge) {
-        C post[(QF + QG) * VEC];
-        const C un = KS ? ScaleOf<C>::inv(p) : C(1);
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-#pragma unroll
-            for (int i = 0; i < QF; ++i) post[i * VEC + k] = KS ? f[i][k] * un : f[i][k];
-#pragma unroll
-            for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = KS ? g[i][k] * un : g[i][k];
-        }
-        edge_writes<DIM, S, VEC, C>(dst, p, x0, y, z, post);
-    }
+    wall_writes<DIM, S, VEC, C, KS>(dst, p, x0, y, z, f, g);
 }
 
 // ROWS consecutive rows per thread, software-pipelined: the loads of the next

@@ -1,53 +1,61 @@
-// Shared-memory staged variant of the fused step (same arithmetic as
-// step_kernel, different data movement).
+// Shared-memory staged variant of the fused step: the same arithmetic as the
+// register kernels (two-relaxation-time form, two nodes per thread on the FP32
+// pair instructions), with the loads done by TMA bulk copies instead of
+// per-thread loads.
 //
 // A persistent CTA walks a list of tiles; a tile is one row segment
-// x in [x0, x0 + tw) of row (y, z).  For every population j the source row
-// segment (shifted by -e_y, -e_z; the x-shift is a shared-memory offset) is
-// copied global -> shared with one cp.async.bulk (TMA bulk copy) that signals an
-// mbarrier with its byte count.  STAGES tiles are in flight per CTA, so the
-// bytes in flight do not depend on the register budget, and the compute reads
-// each node's neighbours from shared memory without shuffles.
+// x in [x0, x0 + tw) of row (y, z).  Warp 0 is the producer: for every
+// population j it copies the source row segment (the row shifted by -e_y, -e_z,
+// widened by A elements on both sides so that the x-shift becomes a
+// shared-memory offset) global -> shared with one cp.async.bulk, completing on
+// the stage's "full" mbarrier; up to `stages` tiles are in flight.  The other NC
+// warps are consumers: each thread pulls the populations of two adjacent nodes
+// from shared memory (compile-time offsets), hands the stage back through its
+// "empty" mbarrier (one arrival per warp), collides the two nodes and stores
+// them with one 2-element store per population (a warp writes 64 consecutive
+// nodes of each plane).
 //
-// Waits are bounded: if a stage does not complete within the iteration budget
-// the CTA records TLBM_ERR_TIMEOUT in a status word and returns.
+// Every wait is bounded in time: a block whose copies do not arrive records
+// TLBM_ERR_TIMEOUT in a status word and returns; the producer warp, and so the
+// block, stays until the copies it issued have landed (again bounded).
 #pragma once
 #include "kernels.cuh"
 
 namespace tlbm {
 
-constexpr int STAGED_THREADS = 256;
-constexpr int STAGED_MIN_BLOCKS = 4;  // 64 registers per thread, 32 warps per SM
-constexpr int STAGED_MAX_STAGES = 8;
-constexpr unsigned STAGED_WAIT_LIMIT = 1u << 22;   // try_wait iterations before giving up
-constexpr unsigned STAGED_DRAIN_LIMIT = 1u << 16;  // second, shorter wait after a timeout
+constexpr int TILE_MAX_STAGES = 8;
+constexpr unsigned long long TILE_WAIT_NS = 200000000;  // give up on a wait after 0.2 s
+constexpr unsigned long long TILE_DRAIN_NS = 10000000;  // and on the drain after 10 ms
 
 struct StagedInfo {
-    int tw;           // tile width (nodes), a multiple of the 16-byte element count
-    int tiles_per_row;
-    long long tiles;  // rows * tiles_per_row
-    int lw;           // shared row length per population (elements) = tw + 2*A
-    int stages;       // tiles in flight per CTA (<= STAGED_MAX_STAGES)
-    int* status;      // device status word (0 ok, 1 timeout)
+    int tw;             // tile width (nodes): a multiple of A, <= 64 NC
+    int tiles_per_row;  // x segments per row
+    int tiles;          // ny * nz * tiles_per_row (< 2^31)
+    int stages;         // tiles in flight per CTA, 2 <= stages <= TILE_MAX_STAGES
+    int* status;        // device status word (0 ok, 1 timeout)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
-
 __device__ __forceinline__ void mbar_fence_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
-
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
@@ -59,7 +67,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-
+// Wait for the phase of `parity` to complete; false after `limit_ns`.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
 // global -> shared bulk copy; both addresses 16-byte aligned, bytes a multiple of 16
 __device__ __forceinline__ void bulk_copy_g2s(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
     asm volatile(
@@ -68,139 +83,219 @@ __device__ __forceinline__ void bulk_copy_g2s(void* sdst, const void* gsrc, uint
         "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
-
-// Issue the copies of tile t into one stage (called by warp 0 only).
-template <int DIM, class S>
-__device__ __forceinline__ void staged_issue(const S* __restrict__ src, const KParams& p, const StagedInfo& si,
-                                             long long t, S* stage, uint64_t* bar) {
-    using LF = typename Lat<DIM>::F;
-    using LG = typename Lat<DIM>::G;
-    constexpr int Q = LF::Q + LG::Q;
-    constexpr int A = 16 / (int)sizeof(S);
-    const Layout& L = p.L;
-    const int lane = threadIdx.x & 31;
-    const long long r = t / si.tiles_per_row;
-    const int x0 = (int)(t - r * si.tiles_per_row) * si.tw;
-    const int y = (int)(r % L.ny);
-    const int z = (int)(r / L.ny);
-    const int tw_eff = min(si.tw, L.nx - x0);
-    // window [x0 - A, end) with end >= x0 + tw_eff + 1, a multiple of A
-    const int end = ((x0 + tw_eff + 1 + A - 1) / A) * A;
-    const uint32_t bytes = (uint32_t)((end - (x0 - A)) * (int)sizeof(S));
-    if (lane == 0) mbar_arrive_expect_tx(bar, bytes * Q);
-    __syncwarp();
-    if (lane < Q) {
-        const S* g = src + L.row(y, z) + p.loff[lane] + (x0 - A);
-        bulk_copy_g2s(stage + (long long)lane * si.lw, g, bytes, bar);
-    }
+// shared -> global bulk copy, same alignment rules
+__device__ __forceinline__ void bulk_copy_s2g(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's shared-memory writes before later bulk copies read them
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// named barrier over n threads (a multiple of 32)
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+// named barrier that also returns whether any of the n threads passed v = true
+__device__ __forceinline__ bool named_sync_or(int id, int n, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.or.pred po, %2, %3, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
 }
 
-template <int DIM, class S, bool TRT>
-__global__ void __launch_bounds__(STAGED_THREADS, STAGED_MIN_BLOCKS) step_staged_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                                     const KParams p, const StagedInfo si) {
+// the value enc_f_k / enc_g_k round to the storage type
+template <class LF, class S, bool KS>
+__device__ __forceinline__ float enc_val_f(float d, int i, float scale) {
+    if constexpr (Storage<S>::offset) return KS ? d : d * scale;
+    else return weight<LF, float>(i) + d;
+}
+template <class S, bool KS>
+__device__ __forceinline__ float enc_val_g(float g, float scale) {
+    if constexpr (Storage<S>::offset) return KS ? g : g * scale;
+    else return g;
+}
+
+template <class S> struct Pair;
+template <> struct Pair<float> {
+    using T = float2;
+    __device__ static float2 unpack(T v) { return v; }
+    __device__ static T pack(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Pair<__half> {
+    using T = __half2;
+    __device__ static float2 unpack(T v) { return __half22float2(v); }
+    __device__ static T pack(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <> struct Pair<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+    __device__ static float2 unpack(T v) { return __bfloat1622float2(v); }
+    __device__ static T pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
+// Stage geometry of a kernel with NC consumer warps: tiles of up to 64 NC nodes,
+// each population row padded by A elements on both sides.
+template <class S, int NC>
+struct TileGeo {
+    static constexpr int A = 16 / (int)sizeof(S);
+    static constexpr int TWMAX = 64 * NC;
+    static constexpr int LW = TWMAX + 2 * A;
+};
+
+template <int DIM, class S, int NC>
+__global__ void __maxnreg__(NC == 8 ? 112 : 168)
+    step_staged_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p, const StagedInfo si) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
-    using C = typename Storage<S>::C;
+    using P2 = Pair<S>;
+    using S2 = typename P2::T;
     constexpr int QF = LF::Q, QG = LG::Q, Q = QF + QG;
-    constexpr int A = 16 / (int)sizeof(S);
+    constexpr int A = TileGeo<S, NC>::A;
+    constexpr int LW = TileGeo<S, NC>::LW;
+    constexpr int STAGE = Q * LW;
+    constexpr bool KS = Storage<S>::offset;  // offset storage: collide the stored, scaled values
     const Layout& L = p.L;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    S* stages = reinterpret_cast<S*>(smem_raw + 128);
-    const long long stage_elems = (long long)Q * si.lw;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + TILE_MAX_STAGES;
+    int4* head = reinterpret_cast<int4*>(empty + TILE_MAX_STAGES);  // per stage: x0, y, z, width
+    S* stages = reinterpret_cast<S*>(smem_raw + 512);
     const int NS = si.stages;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NC);  // one arrival per consumer warp
+        }
         mbar_fence_init();
     }
     __syncthreads();
 
-    const long long G = gridDim.x;
-    // prologue: fill the pipeline
-    if (threadIdx.x < 32) {
-        for (int s = 0; s < NS; ++s) {
-            const long long t = blockIdx.x + s * G;
-            if (t < si.tiles) staged_issue<DIM, S>(src, p, si, t, stages + s * stage_elems, &bars[s]);
-        }
-    }
-
-    const C scale = ScaleOf<C>::s(p);
-    const C inv_scale = ScaleOf<C>::inv(p);
-    long long i = 0;
-    for (long long t = blockIdx.x; t < si.tiles; t += G, ++i) {
-        const int s = (int)(i % NS);
-        const uint32_t parity = (uint32_t)((i / NS) & 1);
-        unsigned spins = 0;
-        bool ok = true;
-        while (!mbar_try_wait(&bars[s], parity)) {
-            if (++spins > STAGED_WAIT_LIMIT) {
-                ok = false;
+    const int G = gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        // producer: tile t = (row r, segment k), row r = (y, z); the tile's
+        // coordinates go to the stage header for the consumers
+        int i = 0;
+        int s = 0, ph = 0;  // stage and the parity of its current use
+        for (int t = blockIdx.x; t < si.tiles; t += G, ++i) {
+            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(ph ^ 1), TILE_WAIT_NS)) {
+                if (lane == 0) atomicExch(si.status, 1);
                 break;
             }
-        }
-        if (__syncthreads_or(!ok)) {
-            // A stage never completed: record it, give the copies still in
-            // flight a short bounded chance to land, and leave as a whole CTA.
-            if (threadIdx.x == 0) {
-                atomicExch(si.status, 1);
-                for (int k = 0; k < NS; ++k) {
-                    const long long tk = t + (long long)k * G;
-                    if (tk >= si.tiles) break;
-                    const int sk = (int)((i + k) % NS);
-                    const uint32_t pk = (uint32_t)(((i + k) / NS) & 1);
-                    unsigned d = 0;
-                    while (!mbar_try_wait(&bars[sk], pk) && ++d < STAGED_DRAIN_LIMIT) {
-                    }
-                }
+            const unsigned r = (unsigned)t / (unsigned)si.tiles_per_row;
+            const int x0 = (t - (int)r * si.tiles_per_row) * si.tw;
+            const unsigned z = r / (unsigned)L.ny;
+            const int y = (int)(r - z * (unsigned)L.ny);
+            const int tw = min(si.tw, L.nx - x0);
+            const int lo = x0 - A;
+            const int end = (x0 + tw + 1 + A - 1) / A * A;  // covers x0 + tw (the right neighbour)
+            const uint32_t bytes = (uint32_t)(end - lo) * (uint32_t)sizeof(S);
+            if (lane == 0) {
+                head[s] = make_int4(x0, y, (int)z, tw);
+                mbar_arrive_expect_tx(&full[s], bytes * Q);
             }
-            __syncthreads();
+            __syncwarp();
+            if (lane < Q)
+                bulk_copy_g2s(stages + s * STAGE + lane * LW, src + L.row(y, (int)z) + p.loff[lane] + lo, bytes,
+                              &full[s]);
+            if (++s == NS) {
+                s = 0;
+                ph ^= 1;
+            }
+        }
+        // the block stays until every copy this warp issued has landed (the
+        // consumers have normally seen them all already)
+        const int issued = i;
+        for (int k = issued > NS ? issued - NS : 0; k < issued; ++k)
+            if (!mbar_wait(&full[k % NS], (uint32_t)((k / NS) & 1), TILE_DRAIN_NS) && lane == 0)
+                atomicExch(si.status, 1);
+        return;
+    }
+
+    // consumers: thread c updates nodes x0 + 2c and x0 + 2c + 1 of each tile
+    const int c = threadIdx.x - 32;
+    const int xr = 2 * c;
+    const float scale = ScaleOf<float>::s(p);
+    const float inv_scale = ScaleOf<float>::inv(p);
+    int s = 0, ph = 0;
+    for (int t = blockIdx.x; t < si.tiles; t += G) {
+        if (!mbar_wait(&full[s], (uint32_t)ph, TILE_WAIT_NS)) {
+            atomicExch(si.status, 1);
             return;
         }
-        const S* st = stages + s * stage_elems;
-        const long long r = t / si.tiles_per_row;
-        const int x0 = (int)(t - r * si.tiles_per_row) * si.tw;
-        const int y = (int)(r % L.ny);
-        const int z = (int)(r / L.ny);
-        const int tw_eff = min(si.tw, L.nx - x0);
-        const long long rowo = L.row(y, z) + x0;
-        const bool edge_row = (y == 0) || (y == L.ny - 1) || (DIM == 3 && (z == 0 || z == L.nz - 1));
-        for (int xr = threadIdx.x; xr < tw_eff; xr += STAGED_THREADS) {
-            C f[QF], g[QG];
+        const int4 hd = head[s];
+        const int x0 = hd.x, y = hd.y, z = hd.z, tw = hd.w;
+        const bool active = xr < tw;
+        const S* st = stages + s * STAGE;
+        float2 fd[QF], gd[QG];
+        if (active) {
             static_for<QF>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
-                const C raw = to_c<C>(st[q * si.lw + A + xr - LF::e(q, 0)]);
-                f[q] = raw_to_dev<LF, S, C>(raw, q, inv_scale);
+                constexpr int ex = LF::e(q, 0);
+                const S* rp = st + q * LW + A + xr - ex;
+                float2 v;
+                if constexpr (ex == 0) v = P2::unpack(*reinterpret_cast<const S2*>(rp));
+                else v = make_float2(to_c<float>(rp[0]), to_c<float>(rp[1]));
+                fd[q] = make_float2(raw_to_dev_k<LF, S, float, KS>(v.x, q, inv_scale),
+                                    raw_to_dev_k<LF, S, float, KS>(v.y, q, inv_scale));
             });
             static_for<QG>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
-                const C raw = to_c<C>(st[(QF + q) * si.lw + A + xr - LG::e(q, 0)]);
-                g[q] = raw_to_g<S, C>(raw, inv_scale);
+                constexpr int ex = LG::e(q, 0);
+                const S* rp = st + (QF + q) * LW + A + xr - ex;
+                float2 v;
+                if constexpr (ex == 0) v = P2::unpack(*reinterpret_cast<const S2*>(rp));
+                else v = make_float2(to_c<float>(rp[0]), to_c<float>(rp[1]));
+                gd[q] = make_float2(raw_to_g_k<S, float, KS>(v.x, inv_scale), raw_to_g_k<S, float, KS>(v.y, inv_scale));
             });
-            collide<DIM, TRT, C>(f, g, p);
-            S* own = dst + rowo + xr;
-            static_for<QF>([&](auto ii) {
-                constexpr int q = decltype(ii)::value;
-                own[p.soff[q]] = enc_f<LF, S, C>(f[q], q, scale);
-            });
-            static_for<QG>([&](auto ii) {
-                constexpr int q = decltype(ii)::value;
-                own[p.soff[QF + q]] = enc_g<S, C>(g[q], scale);
-            });
-            const int x = x0 + xr;
-            if (edge_row || x == 0 || x == L.nx - 1) {
-                C post[Q];
-#pragma unroll
-                for (int q = 0; q < QF; ++q) post[q] = f[q];
-#pragma unroll
-                for (int q = 0; q < QG; ++q) post[QF + q] = g[q];
-                edge_writes<DIM, S, 1, C>(dst, p, x, y, z, post);
-            }
         }
-        __syncthreads();  // every thread is done with stage s
-        const long long tn = t + (long long)NS * G;
-        if (threadIdx.x < 32 && tn < si.tiles)
-            staged_issue<DIM, S>(src, p, si, tn, stages + s * stage_elems, &bars[s]);
+        // this warp is done with stage s
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == NS) {
+            s = 0;
+            ph ^= 1;
+        }
+        if (!active) continue;
+        collide_trt_v<DIM, float2, KS>(fd, gd, p);
+        S* own = dst + L.row(y, z) + x0 + xr;
+        if (xr + 1 < tw) {
+            static_for<QF>([&](auto ii) {
+                constexpr int q = decltype(ii)::value;
+                *reinterpret_cast<S2*>(own + p.soff[q]) =
+                    P2::pack(enc_val_f<LF, S, KS>(fd[q].x, q, scale), enc_val_f<LF, S, KS>(fd[q].y, q, scale));
+            });
+            static_for<QG>([&](auto ii) {
+                constexpr int q = decltype(ii)::value;
+                *reinterpret_cast<S2*>(own + p.soff[QF + q]) =
+                    P2::pack(enc_val_g<S, KS>(gd[q].x, scale), enc_val_g<S, KS>(gd[q].y, scale));
+            });
+        } else {
+            static_for<QF>([&](auto ii) {
+                constexpr int q = decltype(ii)::value;
+                own[p.soff[q]] = enc_f_k<LF, S, float, KS>(fd[q].x, q, scale);
+            });
+            static_for<QG>([&](auto ii) {
+                constexpr int q = decltype(ii)::value;
+                own[p.soff[QF + q]] = enc_g_k<S, float, KS>(gd[q].x, scale);
+            });
+        }
+        float f2[QF][2], g2[QG][2];
+#pragma unroll
+        for (int q = 0; q < QF; ++q) { f2[q][0] = fd[q].x; f2[q][1] = fd[q].y; }
+#pragma unroll
+        for (int q = 0; q < QG; ++q) { g2[q][0] = gd[q].x; g2[q][1] = gd[q].y; }
+        wall_writes<DIM, S, 2, float, KS>(dst, p, x0 + xr, y, z, f2, g2);
     }
 }
 

@@ -122,9 +122,10 @@ def test_one_step_random_populations(T, O, prec, lattice, shape, walls, pm):
     variants = [("reg", v, f, 1) for v, f in VARIANTS[(lattice, prec)]]
     variants += [("reg", v, 2, r) for v, r in ROW_VARIANTS[(lattice, prec)]]
     if prec != FP64:
-        # shared-memory staged kernel: several tiles per row, 2 and 3 stages
+        # shared-memory staged kernel: several tiles per row, 3 and 4 stages, and
+        # whole rows
         A = 16 // (4 if prec == FP32 else 2)
-        variants += [("staged", A, 2, 0), ("staged", 2 * A, 3, 0)]
+        variants += [("staged", A, 3, 0), ("staged", 2 * A, 4, 0), ("staged", 0, 0, 0)]
     for kind, vec, form, rows in variants:
         g = T.Sim(nx, ny, nz, lattice=lattice, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec, **kw)
         if kind == "staged":
@@ -165,7 +166,7 @@ def test_variants_agree_bitwise(T):
                 g.step(20)
                 outs.append(g.get_populations())
                 g.close()
-        for tw, ns in ((0, 0), (16, 2), (64, 5)):
+        for tw, ns in ((0, 0), (16, 3), (64, 4), (256, 0), (512, 2)):
             g = T.Sim(*shape, lattice=lattice, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
             g.set_staged(tw, ns)
             g.init(11, 1e-3)
