@@ -75,6 +75,16 @@ enum tlbm_walls { TLBM_RB = 0, TLBM_SIDE_HEATED = 1 };
 /* Output element type for tlbm_macros. */
 enum tlbm_dtype { TLBM_OUT_F64 = 0, TLBM_OUT_F32 = 1 };
 
+/* Streaming scheme (the same method, two memory layouts).  PULL: two population
+ * buffers, each step reads one and writes the other.  INPLACE: one buffer,
+ * steps alternate between a half that reads and writes every node's own slots
+ * (storing each post-collision value in the slot of the opposite direction) and
+ * a half that reads from the neighbours and writes to them (the "AA" access
+ * pattern); the same bytes per lattice update, half the device memory.  The
+ * in-place scheme runs on the register kernels only (tlbm_set_staged and
+ * multi-row variants return TLBM_ERR_UNSUPPORTED) and not in batches. */
+enum tlbm_streaming { TLBM_STREAM_PULL = 0, TLBM_STREAM_INPLACE = 1 };
+
 /* Optional parameters.  Initialise with tlbm_default_params(); every double left
  * as NaN is derived from (Ra, Pr, Ma) as stated at the top of this file:
  *   s_nu = 1/(3 nu + 1/2) on all even non-conserved flow moments (s_e, s_eps, s_pi),
@@ -95,6 +105,7 @@ typedef struct {
     double body_force[3];
     double Th, Tc;
     double store_scale;     /* FP16/BF16 storage scale (power of two); NaN = default */
+    int streaming;          /* TLBM_STREAM_PULL (0, default) or TLBM_STREAM_INPLACE */
 } tlbm_params;
 
 typedef struct tlbm_s* tlbm_t;

@@ -49,6 +49,14 @@ static int cuda_fail(tlbm_t h, cudaError_t e, const char* what) {
 static void drop_graph(tlbm_t h);
 static int set_staged(tlbm_t h, int tile_width, int stages);
 
+// The buffer (two-buffer pull) or the order (in place: 0 natural, 1 swapped)
+// of the current state, and the matching state order for the diagnostic and
+// transfer kernels.
+static void set_cur(tlbm_t h, int c) {
+    h->cur = c;
+    h->kp.state = h->aa ? (c ? 2 : 1) : 0;
+}
+
 #define TLBM_CHECK_HANDLE(h)                                   \
     do {                                                       \
         if (!(h)) return fail(nullptr, TLBM_ERR_ARG, "NULL handle"); \
@@ -93,7 +101,7 @@ __device__ __forceinline__ void node_xyz(long long n, const Layout& L, int& x, i
 
 // Initial state: f = w (rho = 1, u = 0), g = g_eq(T, 0) with the conductive
 // profile plus seeded uniform noise.  Every pre-collision value f_i(x) is
-// written into the slot x - e_i it is pulled from.
+// written where the state order p.state keeps it (pre_index).
 template <int DIM, class S>
 __global__ void init_kernel(S* __restrict__ buf, const KParams p, uint64_t seed, double amp) {
     using LF = typename Lat<DIM>::F;
@@ -119,20 +127,20 @@ __global__ void init_kernel(S* __restrict__ buf, const KParams p, uint64_t seed,
         const C scale = (C)p.scale;
         static_for<LF::Q>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            buf[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))] =
+            buf[pre_index<LF, i>(p, x, y, z)] =
                 enc_f<LF, S, C>(C(0), i, scale);
         });
         S* gb = buf + (long long)LF::Q * L.plane;
         static_for<LG::Q>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            gb[(long long)i * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))] =
+            gb[pre_index<LG, i>(p, x, y, z)] =
                 enc_g<S, C>((C)gq[i], scale);
         });
     }
 }
 
 // Initial state from given fields (warm start): f = f_eq(rho = 1, u) and
-// g = g_eq(T, u) at every node, written into the slots they are pulled from.
+// g = g_eq(T, u) at every node, written where p.state keeps them.
 template <int DIM, class S>
 __global__ void init_fields_kernel(S* __restrict__ buf, const KParams p, const float* __restrict__ Tf,
                                    const float* __restrict__ uxf, const float* __restrict__ uyf,
@@ -164,19 +172,19 @@ __global__ void init_fields_kernel(S* __restrict__ buf, const KParams p, const f
             constexpr int i = decltype(ii)::value;
             const double eu = LF::e(i, 0) * u[0] + LF::e(i, 1) * u[1] + LF::e(i, 2) * u[2];
             const double dev = (LF::w36(i) / 36.0) * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-            buf[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))] =
+            buf[pre_index<LF, i>(p, x, y, z)] =
                 enc_f<LF, S, C>((C)dev, i, scale);
         });
         S* gb = buf + (long long)LF::Q * L.plane;
         static_for<LG::Q>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            gb[(long long)i * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))] =
+            gb[pre_index<LG, i>(p, x, y, z)] =
                 enc_g<S, C>((C)gq[i], scale);
         });
     }
 }
 
-// Host FP64 populations (one plane, nodes [n0, n0 + cnt)) -> pull slots.
+// Host FP64 populations (one plane, nodes [n0, n0 + cnt)) -> the state's slots.
 template <int DIM, class S>
 __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ stage, int pop, long long n0,
                                long long cnt, const Window w, const KParams p) {
@@ -195,7 +203,7 @@ __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ s
                 S s;
                 if constexpr (Storage<S>::offset) s = from_c<S>((C)((v - LF::w36(i) / 36.0) * p.scale));
                 else s = (S)v;
-                buf[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))] = s;
+                buf[pre_index<LF, i>(p, x, y, z)] = s;
             }
         });
         static_for<LG::Q>([&](auto ii) {
@@ -204,13 +212,13 @@ __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ s
                 S s;
                 if constexpr (Storage<S>::offset) s = from_c<S>((C)(v * p.scale));
                 else s = (S)v;
-                buf[(long long)(LF::Q + i) * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))] = s;
+                buf[(long long)LF::Q * L.plane + pre_index<LG, i>(p, x, y, z)] = s;
             }
         });
     }
 }
 
-// Pull slots -> canonical FP64 populations (one plane, nodes [n0, n0 + cnt)).
+// The state's slots -> canonical FP64 populations (one plane, nodes [n0, n0 + cnt)).
 template <int DIM, class S>
 __global__ void gather_kernel(const S* __restrict__ buf, double* __restrict__ stage, int pop, long long n0,
                               long long cnt, const Window w, const KParams p) {
@@ -226,7 +234,7 @@ __global__ void gather_kernel(const S* __restrict__ buf, double* __restrict__ st
             constexpr int i = decltype(ii)::value;
             if (pop == i) {
                 const double raw = to_c<double>(
-                    buf[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))]);
+                    buf[pre_index<LF, i>(p, x, y, z)]);
                 if constexpr (Storage<S>::offset) v = LF::w36(i) / 36.0 + raw * (double)p.inv_scale;
                 else v = raw;
             }
@@ -235,7 +243,7 @@ __global__ void gather_kernel(const S* __restrict__ buf, double* __restrict__ st
             constexpr int i = decltype(ii)::value;
             if (pop == LF::Q + i) {
                 const double raw = to_c<double>(
-                    buf[(long long)(LF::Q + i) * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))]);
+                    buf[(long long)LF::Q * L.plane + pre_index<LG, i>(p, x, y, z)]);
                 if constexpr (Storage<S>::offset) v = raw * (double)p.inv_scale;
                 else v = raw;
             }
@@ -455,6 +463,8 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
         return fail(nullptr, TLBM_ERR_ARG, "unknown walls %d", prm.walls);
     if (prm.periodic_mask < 0 || prm.periodic_mask > 7)
         return fail(nullptr, TLBM_ERR_ARG, "periodic_mask out of range");
+    if (prm.streaming != TLBM_STREAM_PULL && prm.streaming != TLBM_STREAM_INPLACE)
+        return fail(nullptr, TLBM_ERR_ARG, "unknown streaming %d", prm.streaming);
 
     tlbm_s* h = new (std::nothrow) tlbm_s();
     if (!h) return fail(nullptr, TLBM_ERR_OOM, "host allocation failed");
@@ -546,16 +556,21 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
         const long long P = kp.L.P, RP = (long long)(ny + 2) * kp.L.P;
         const int qf = h->qf;
         for (int j = 0; j < h->qf + h->qg; ++j) {
-            int ey, ez;
+            int ey, ez, jo;  // jo: the opposite direction's plane
             if (dim == 2) {
                 ey = j < qf ? D2Q9::e(j, 1) : D2Q5::e(j - qf, 1);
                 ez = 0;
+                jo = j < qf ? D2Q9::opp(j) : qf + D2Q5::opp(j - qf);
             } else {
                 ey = j < qf ? D3Q19::e(j, 1) : D3Q7::e(j - qf, 1);
                 ez = j < qf ? D3Q19::e(j, 2) : D3Q7::e(j - qf, 2);
+                jo = j < qf ? D3Q19::opp(j) : qf + D3Q7::opp(j - qf);
             }
             kp.soff[j] = (int)((long long)j * kp.L.plane);
             kp.loff[j] = (int)((long long)j * kp.L.plane - ey * P - ez * RP);
+            // in-place second half: read x - e_j of plane jbar, push to x + e_j of plane j
+            kp.oload[j] = (int)((long long)jo * kp.L.plane - ey * P - ez * RP);
+            kp.ostore[j] = (int)((long long)j * kp.L.plane + ey * P + ez * RP);
         }
     }
     h->vec = default_variant(dim, precision).vec;
@@ -598,14 +613,17 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
     }
     h->elem = precision == TLBM_FP64 ? 8 : (precision == TLBM_FP32 ? 4 : 2);
     h->popset_bytes = align_up((size_t)(h->qf + h->qg) * (size_t)kp.L.plane * h->elem, 256);
-    h->red_off = 2 * h->popset_bytes;
+    h->aa = prm.streaming == TLBM_STREAM_INPLACE;
+    h->nbuf = h->aa ? 1 : 2;
+    if (h->aa) h->rows = 1;  // the in-place halves have no multi-row variant
+    h->red_off = h->nbuf * h->popset_bytes;
     h->res_off = h->red_off + align_up((size_t)RED_BLOCKS * RED_FIELDS * sizeof(double), 256);
     h->status_off = h->res_off + 128;
     h->stage_off = h->res_off + 256;
     const long long N = (long long)nx * ny * nz;
     h->total_bytes = h->stage_off + align_up((size_t)std::min<long long>(N, STAGE_NODES) * sizeof(double), 256);
     h->stream = nullptr;
-    h->cur = 0;
+    set_cur(h, 0);
     h->t = 0;
     h->graph_steps = 16;
     *out = h;
@@ -637,12 +655,12 @@ extern "C" int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes) {
     h->mem = (char*)dev_ptr;
     h->mem_bytes = bytes;
     h->buf[0] = h->mem;
-    h->buf[1] = h->mem + h->popset_bytes;
-    h->cur = 0;
+    h->buf[1] = h->aa ? h->mem : h->mem + h->popset_bytes;
+    set_cur(h, 0);
     // 2D FP16/BF16 storage with two-relaxation-time rates defaults to the
     // shared-memory staged kernel (512-node tiles, 3 stages: the fastest on
     // GB300); the register kernel stays if the device cannot host it
-    if (!h->variant_chosen && h->dim == 2 && (h->prec == TLBM_FP16_OFFSET || h->prec == TLBM_BF16_OFFSET) &&
+    if (!h->variant_chosen && !h->aa && h->dim == 2 && (h->prec == TLBM_FP16_OFFSET || h->prec == TLBM_BF16_OFFSET) &&
         h->kp.trt && set_staged(h, 512, 3) != TLBM_OK) {
         h->staged = 0;
         h->err[0] = 0;
@@ -660,11 +678,11 @@ extern "C" int tlbm_init(tlbm_t h, uint64_t seed, double noise_amp) {
     TLBM_CHECK_HANDLE(h);
     TLBM_CHECK_BOUND(h);
     if (!std::isfinite(noise_amp) || noise_amp < 0) return fail(h, TLBM_ERR_ARG, "noise_amp must be finite, >= 0");
-    cudaError_t e = cudaMemsetAsync(h->mem, 0, 2 * h->popset_bytes, h->stream);
+    cudaError_t e = cudaMemsetAsync(h->mem, 0, h->nbuf * h->popset_bytes, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     e = cudaMemsetAsync(h->mem + h->status_off, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-    h->cur = 0;
+    set_cur(h, 0);
     e = with_types(h->dim, h->prec, [&](auto K) { return decltype(K)::init(h->buf[0], h->kp, seed, noise_amp, h->stream); });
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
     h->launches += 1;
@@ -676,10 +694,10 @@ extern "C" int tlbm_init_fields(tlbm_t h, const float* T, const float* ux, const
     TLBM_CHECK_HANDLE(h);
     TLBM_CHECK_BOUND(h);
     if (!T) return fail(h, TLBM_ERR_ARG, "T is required");
-    cudaError_t e = cudaMemsetAsync(h->mem, 0, 2 * h->popset_bytes, h->stream);
+    cudaError_t e = cudaMemsetAsync(h->mem, 0, h->nbuf * h->popset_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->mem + h->status_off, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-    h->cur = 0;
+    set_cur(h, 0);
     e = with_types(h->dim, h->prec, [&](auto K) {
         return decltype(K)::init_fields(h->buf[0], h->kp, T, ux, uy, uz, h->stream);
     });
@@ -709,6 +727,9 @@ static cudaError_t launch_step_raw(tlbm_t h, int parity, cudaStream_t s) {
     const int threads_x = (h->nx + vec - 1) / vec;
     dim3 block(bx, by, 1);
     dim3 grid((threads_x + bx - 1) / bx, (h->ny + by * rows - 1) / (by * rows), h->dim == 3 ? h->nz : 1);
+    // in place: natural order -> the AA_EVEN half, swapped -> AA_ODD, one buffer
+    if (h->aa) return launch_step(h->dim, h->prec, vec, h->trt != 0, parity ? -AA_ODD : -AA_EVEN, src, h->buf[0], kp,
+                                  grid, block, s);
     return launch_step(h->dim, h->prec, vec, h->trt != 0, rows, src, dst, kp, grid, block, s);
 }
 
@@ -748,7 +769,7 @@ static int build_graph(tlbm_t h) {
 static cudaError_t launch_one_step(tlbm_t h) {
     cudaError_t e = launch_step_raw(h, h->cur, h->stream);
     if (e == cudaSuccess) {
-        h->cur ^= 1;
+        set_cur(h, h->cur ^ 1);
         h->t += 1;
         h->launches += 1;
     }
@@ -908,11 +929,11 @@ extern "C" int tlbm_set_populations(tlbm_t h, const double* host_f, const double
     const long long N = (long long)h->nx * h->ny * h->nz;
     const Window full = {0, 0, 0, h->nx, h->ny, h->nz};
     double* stage = (double*)(h->mem + h->stage_off);
-    cudaError_t e = cudaMemsetAsync(h->mem, 0, 2 * h->popset_bytes, h->stream);
+    cudaError_t e = cudaMemsetAsync(h->mem, 0, h->nbuf * h->popset_bytes, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     e = cudaMemsetAsync(h->mem + h->status_off, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-    h->cur = 0;
+    set_cur(h, 0);
     for (int pop = 0; pop < h->qf + h->qg; ++pop) {
         const double* srcp = pop < h->qf ? host_f + (long long)pop * N : host_g + (long long)(pop - h->qf) * N;
         for (long long n0 = 0; n0 < N; n0 += STAGE_NODES) {
@@ -943,15 +964,20 @@ extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bl
     const int by = block_y > 0 ? block_y : default_variant(h->dim, h->prec).by;
     if (bx % 32 || bx * by > 1024) return fail(h, TLBM_ERR_ARG, "block_x must be a multiple of 32, bx*by <= 1024");
     const int nr = rows > 0 ? rows : 1;
-    if (!step_variant_available(h->dim, h->prec, v, trt != 0, nr))
-        return fail(h, TLBM_ERR_UNSUPPORTED, "step variant (vec %d, %s, %d rows) not built", v, trt ? "TRT" : "MRT",
-                    nr);
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, step_function(h->dim, h->prec, v, trt != 0, nr));
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncGetAttributes");
-    if (bx * by > fa.maxThreadsPerBlock)
-        return fail(h, TLBM_ERR_ARG, "block of %d threads exceeds the variant's limit of %d", bx * by,
-                    fa.maxThreadsPerBlock);
+    if (h->aa && nr != 1) return fail(h, TLBM_ERR_UNSUPPORTED, "in-place streaming has no multi-row variant");
+    // the in-place scheme alternates two kernels; both must exist
+    const int kinds[2] = {h->aa ? -AA_EVEN : nr, h->aa ? -AA_ODD : nr};
+    for (int kind : kinds) {
+        if (!step_variant_available(h->dim, h->prec, v, trt != 0, kind))
+            return fail(h, TLBM_ERR_UNSUPPORTED, "step variant (vec %d, %s, %d rows%s) not built", v,
+                        trt ? "TRT" : "MRT", nr, h->aa ? ", in place" : "");
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, step_function(h->dim, h->prec, v, trt != 0, kind));
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncGetAttributes");
+        if (bx * by > fa.maxThreadsPerBlock)
+            return fail(h, TLBM_ERR_ARG, "block of %d threads exceeds the variant's limit of %d", bx * by,
+                        fa.maxThreadsPerBlock);
+    }
     h->vec = v;
     h->trt = trt;
     h->bx = bx;
@@ -965,6 +991,7 @@ extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bl
 }
 
 static int set_staged(tlbm_t h, int tile_width, int stages) {
+    if (h->aa) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel uses two buffers (no in-place variant)");
     if (h->prec == TLBM_FP64) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel has no FP64 variant");
     if (!h->kp.trt) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel needs two-relaxation-time rates");
     const int A = 16 / (int)h->elem;

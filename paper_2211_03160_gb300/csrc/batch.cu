@@ -209,6 +209,8 @@ extern "C" int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* 
     if (!out) return bfail(nullptr, TLBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > 65536 || !instances) return bfail(nullptr, TLBM_ERR_ARG, "need 1..65536 instances");
+    if (p && p->streaming != TLBM_STREAM_PULL)
+        return bfail(nullptr, TLBM_ERR_UNSUPPORTED, "batched ensembles use two-buffer streaming");
     tlbm_batch_s* b = new (std::nothrow) tlbm_batch_s();
     if (!b) return bfail(nullptr, TLBM_ERR_OOM, "host allocation failed");
     b->n = n;

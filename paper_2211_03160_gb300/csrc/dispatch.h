@@ -12,7 +12,9 @@ namespace tlbm {
 // prec: 0 FP64, 1 FP32, 2 FP16-offset, 3 BF16-offset (enum tlbm_prec).
 // vec: nodes per thread.  trt: two-relaxation-time form of the collision.
 // Returns cudaErrorInvalidValue if the variant is not compiled.
-// rows: consecutive rows per thread (1, or 2 / 4 for the software-pipelined kernel).
+// rows: consecutive rows per thread (1, or 2 / 4 for the software-pipelined kernel);
+// -AA_EVEN / -AA_ODD select the two halves of an in-place step pair, which read
+// and write `dst` only.
 cudaError_t launch_step(int dim, int prec, int vec, bool trt, int rows, const void* src, void* dst,
                         const KParams& p, dim3 grid, dim3 block, cudaStream_t s);
 bool step_variant_available(int dim, int prec, int vec, bool trt, int rows);
@@ -62,3 +64,19 @@ const void* func_step_f64(int dim, int vec, bool trt, int rows);
     }
 #define TLBM_ROWS_FUNC(DIM, S, VEC, ROWS) \
     if (vec == VEC && trt && rows == ROWS) return (const void*)&tlbm::step_kernel_rows<DIM, S, VEC, true, ROWS>;
+
+// in-place (AA) halves
+#define TLBM_AA_CASE(DIM, S, VEC, TRT)                                                                       \
+    if (vec == VEC && trt == TRT && rows == -tlbm::AA_EVEN) {                                               \
+        tlbm::step_kernel_aa<DIM, S, VEC, TRT, tlbm::AA_EVEN><<<grid, block, 0, s>>>((S*)dst, p);           \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    if (vec == VEC && trt == TRT && rows == -tlbm::AA_ODD) {                                                \
+        tlbm::step_kernel_aa<DIM, S, VEC, TRT, tlbm::AA_ODD><<<grid, block, 0, s>>>((S*)dst, p);            \
+        return cudaGetLastError();                                                                          \
+    }
+#define TLBM_AA_FUNC(DIM, S, VEC, TRT)                                                                       \
+    if (vec == VEC && trt == TRT && rows == -tlbm::AA_EVEN)                                                 \
+        return (const void*)&tlbm::step_kernel_aa<DIM, S, VEC, TRT, tlbm::AA_EVEN>;                         \
+    if (vec == VEC && trt == TRT && rows == -tlbm::AA_ODD)                                                  \
+        return (const void*)&tlbm::step_kernel_aa<DIM, S, VEC, TRT, tlbm::AA_ODD>;

@@ -16,6 +16,8 @@ struct tlbm_s {
     tlbm::KParams kp;
     int vec, trt, bx, by;      // step kernel variant and block shape
     int rows;                  // consecutive rows per thread (software-pipelined when > 1)
+    int aa;                    // 1: in-place (AA) streaming in one population buffer
+    int nbuf;                  // population buffers: 2, or 1 in place
     int graph_steps;           // steps per CUDA graph replay in tlbm_step (0: plain launches)
     cudaGraphExec_t graph;     // captured block of graph_steps steps starting from buffer 0
     cudaStream_t capture_stream;
@@ -30,7 +32,7 @@ struct tlbm_s {
     char* mem;                 // bound device block
     size_t mem_bytes;
     void* buf[2];
-    int cur;                   // buffer holding the current state
+    int cur;                   // buffer holding the current state (in place: 0 natural, 1 swapped order)
     int64_t t;
     cudaStream_t stream;
     int64_t launches;

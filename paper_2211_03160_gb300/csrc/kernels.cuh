@@ -74,6 +74,17 @@ struct KParams {
     // (32-bit: a population set holds fewer than 2^31 elements)
     int loff[2 * MAXQ];
     int soff[2 * MAXQ];
+    // in-place (AA) streaming, second half of a step pair: element offsets,
+    // relative to a node's own slot in plane 0, of the slot population j is read
+    // from (x - e_j in plane jbar) and of the target row it is pushed to
+    // (x + e_j in plane j; the x-shift is taken by the kernel's stores)
+    int oload[2 * MAXQ];
+    int ostore[2 * MAXQ];
+    // where the state's pre-collision f_i(x) lives, for the diagnostic and
+    // transfer kernels: 0 two-buffer pull layout (slot x - e_i of plane i),
+    // 1 in-place natural order (slot x of plane i), 2 in-place swapped order
+    // (slot x - e_i of plane ibar)
+    int state;
 };
 
 // ------------------------------------------------------------------ storage
@@ -696,10 +707,24 @@ __device__ __forceinline__ void pull_row(const S* __restrict__ q, int lane, C (&
 
 // ------------------------------------------------------------------ wall rules
 
+// Streaming schemes (the MODE of the wall rules and of the step body):
+//   PULL    two buffers; slot (s, i) holds what node s + e_i pulls next step.
+//   AA_EVEN in place, first half of a step pair: every node reads its own slots
+//           (x, i), collides, and writes f+_i back into its own slot (x, ibar).
+//   AA_ODD  in place, second half: node x reads f_i from (x - e_i, ibar), collides
+//           and pushes f+_i to (x + e_i, i), which restores the natural order.
+// In both in-place halves every node reads and writes one and the same set of
+// slots, so the update is race-free in a single buffer.
+constexpr int PULL = 0, AA_EVEN = 1, AA_ODD = 2;
+
 // Write the post-collision value `val` of population i (set LS, flow or
-// thermal) of node (x, y, z) into the ghost slot that will pull it, if it
-// leaves the cell.  THERMAL selects the temperature rules of §2.2.
-template <class LS, bool THERMAL, int i, class S, class C>
+// thermal) of node (x, y, z) where the next step will read it, if it leaves
+// the cell.  THERMAL selects the temperature rules of §2.2.  PULL: into the
+// ghost slot the node (wall) or its periodic image pulls from.  AA_EVEN: into
+// the ghost slot the following AA_ODD half reads it from.  AA_ODD: into the slot
+// the next AA_EVEN half reads (the node's own slot of the opposite direction
+// for a wall, the image's own slot for a periodic face).
+template <class LS, bool THERMAL, int i, class S, class C, int MODE = PULL>
 __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams& p, int x, int y, int z, C val,
                                             C scale) {
     constexpr int ex = LS::e(i, 0), ey = LS::e(i, 1), ez = LS::e(i, 2);
@@ -711,9 +736,9 @@ __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams&
     const bool oz = (ez != 0) && (dz < 0 || dz >= L.nz);
     if (!(ox || oy || oz)) return;
     const bool wall = (ox && !(p.periodic & 1)) || (oy && !(p.periodic & 2)) || (oz && !(p.periodic & 4));
+    constexpr int o = LS::opp(i);
     if (wall) {
-        // bounce-back into the node's own pull slot for the opposite direction
-        constexpr int o = LS::opp(i);
+        // bounce-back: the value returns to the node as f_ibar of the next step
         C out = val;
         if constexpr (THERMAL) {
             // axis-aligned: exactly one axis is crossed
@@ -723,18 +748,27 @@ __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams&
                 const C Tw = hi ? PV<C>::Tc(p) : PV<C>::Th(p);
                 out = -val + PV<C>::omega(p) * Tw;  // anti-bounce-back
             }
-            base[(long long)o * L.plane + L.slot(dx, dy, dz)] = enc_g<S, C>(out, scale);
-        } else {
-            base[(long long)o * L.plane + L.slot(dx, dy, dz)] = enc_f<LS, S, C>(out, o, scale);
         }
+        // written by PULL: slot (x + e_i) of plane ibar, where the node pulls
+        // ibar from; by AA_EVEN: slot (x + e_i) of plane i, where the next
+        // AA_ODD half reads it; by AA_ODD: the node's own slot of plane ibar,
+        // where the next AA_EVEN half reads it
+        constexpr int plane = MODE == AA_EVEN ? i : o;
+        const long long s = MODE == AA_ODD ? L.slot(x, y, z) : L.slot(dx, dy, dz);
+        if constexpr (THERMAL) base[(long long)plane * L.plane + s] = enc_g<S, C>(out, scale);
+        else base[(long long)plane * L.plane + s] = enc_f<LS, S, C>(out, plane, scale);
     } else {
-        // periodic: the image node wrap(d) pulls from wrap(d) - e_i
+        // periodic: the value reaches the image node w = wrap(x + e_i) as f_i;
+        // written by PULL: slot (w - e_i) of plane i; by AA_EVEN: slot (w - e_i)
+        // of plane ibar (the next AA_ODD half reads there); by AA_ODD: w's own
+        // slot of plane i (the next AA_EVEN half reads there)
         const int wx = ox ? (dx < 0 ? dx + L.nx : dx - L.nx) : dx;
         const int wy = oy ? (dy < 0 ? dy + L.ny : dy - L.ny) : dy;
         const int wz = oz ? (dz < 0 ? dz + L.nz : dz - L.nz) : dz;
-        const long long s = L.slot(wx - ex, wy - ey, wz - ez);
-        if constexpr (THERMAL) base[(long long)i * L.plane + s] = enc_g<S, C>(val, scale);
-        else base[(long long)i * L.plane + s] = enc_f<LS, S, C>(val, i, scale);
+        constexpr int plane = MODE == AA_EVEN ? o : i;
+        const long long s = MODE == AA_ODD ? L.slot(wx, wy, wz) : L.slot(wx - ex, wy - ey, wz - ez);
+        if constexpr (THERMAL) base[(long long)plane * L.plane + s] = enc_g<S, C>(val, scale);
+        else base[(long long)plane * L.plane + s] = enc_f<LS, S, C>(val, plane, scale);
     }
 }
 
@@ -801,7 +835,7 @@ __device__ __forceinline__ void pull_node_vec(const S* __restrict__ own, const K
 // Wall and periodic rules for the nodes of a thread at the edge of the cell.
 // Kept out of line: only edge threads call it, and its fully unrolled body
 // would otherwise crowd the instruction cache of the hot path.
-template <int DIM, class S, int VEC, class C>
+template <int DIM, class S, int VEC, class C, int MODE = PULL>
 __device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, int x0, int y, int z,
                                          const C* __restrict__ post) {
     using LF = typename Lat<DIM>::F;
@@ -814,11 +848,11 @@ __device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, 
         if (x >= p.L.nx) break;
         static_for<QF>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            ghost_write<LF, false, i, S, C>(dst, p, x, y, z, post[i * VEC + k], scale);
+            ghost_write<LF, false, i, S, C, MODE>(dst, p, x, y, z, post[i * VEC + k], scale);
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            ghost_write<LG, true, i, S, C>(gdst, p, x, y, z, post[(QF + i) * VEC + k], scale);
+            ghost_write<LG, true, i, S, C, MODE>(gdst, p, x, y, z, post[(QF + i) * VEC + k], scale);
         });
     }
 }
@@ -826,7 +860,7 @@ __device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, 
 // The populations with e_x = SIDE of node k of a thread's VEC nodes, for a node
 // on the x face SIDE of an inner row (y, z away from the faces) with x not
 // periodic: those, and only those, leave the cell, through that face.
-template <class LS, bool THERMAL, int SIDE, class S, int VEC, class C, bool KS>
+template <class LS, bool THERMAL, int SIDE, class S, int VEC, class C, bool KS, int MODE = PULL>
 __device__ __forceinline__ void x_face(S* __restrict__ base, const KParams& p, int x, int y, int z, int k,
                                        const C (&v)[LS::Q][VEC]) {
     const C scale = ScaleOf<C>::s(p);
@@ -838,7 +872,7 @@ __device__ __forceinline__ void x_face(S* __restrict__ base, const KParams& p, i
 #pragma unroll
             for (int kk = 1; kk < VEC; ++kk)
                 if (k == kk) val = v[i][kk];
-            ghost_write<LS, THERMAL, i, S, C>(base, p, x, y, z, KS ? val * un : val, scale);
+            ghost_write<LS, THERMAL, i, S, C, MODE>(base, p, x, y, z, KS ? val * un : val, scale);
         }
     });
 }
@@ -847,7 +881,7 @@ __device__ __forceinline__ void x_face(S* __restrict__ base, const KParams& p, i
 // Threads holding x = 0 or x = nx - 1 of an inner row only have the x-face
 // populations to place (inline); rows on a y or z face, and periodic x, take the
 // general out-of-line path.
-template <int DIM, class S, int VEC, class C, bool KS>
+template <int DIM, class S, int VEC, class C, bool KS, int MODE = PULL>
 __device__ __forceinline__ void wall_writes(S* __restrict__ dst, const KParams& p, int x0, int y, int z,
                                             const C (&f)[Lat<DIM>::F::Q][VEC], const C (&g)[Lat<DIM>::G::Q][VEC]) {
     using LF = typename Lat<DIM>::F;
@@ -866,18 +900,18 @@ __device__ __forceinline__ void wall_writes(S* __restrict__ dst, const KParams& 
 #pragma unroll
             for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = KS ? g[i][k] * un : g[i][k];
         }
-        edge_writes<DIM, S, VEC, C>(dst, p, x0, y, z, post);
+        edge_writes<DIM, S, VEC, C, MODE>(dst, p, x0, y, z, post);
         return;
     }
     S* __restrict__ gdst = dst + (long long)QF * L.plane;
     if (xlo) {
-        x_face<LF, false, -1, S, VEC, C, KS>(dst, p, 0, y, z, 0, f);
-        x_face<LG, true, -1, S, VEC, C, KS>(gdst, p, 0, y, z, 0, g);
+        x_face<LF, false, -1, S, VEC, C, KS, MODE>(dst, p, 0, y, z, 0, f);
+        x_face<LG, true, -1, S, VEC, C, KS, MODE>(gdst, p, 0, y, z, 0, g);
     }
     if (xhi) {
         const int k = L.nx - 1 - x0;
-        x_face<LF, false, 1, S, VEC, C, KS>(dst, p, L.nx - 1, y, z, k, f);
-        x_face<LG, true, 1, S, VEC, C, KS>(gdst, p, L.nx - 1, y, z, k, g);
+        x_face<LF, false, 1, S, VEC, C, KS, MODE>(dst, p, L.nx - 1, y, z, k, f);
+        x_face<LG, true, 1, S, VEC, C, KS, MODE>(gdst, p, L.nx - 1, y, z, k, g);
     }
 }
 
@@ -943,6 +977,160 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
 
     // wall and periodic rules for values that leave the cell
     wall_writes<DIM, S, VEC, C, KS>(dst, p, x0, y, z, f, g);
+}
+
+// ------------------------------------------------------------------ in-place (AA) streaming
+
+// Push the post-collision values v[k] of nodes x0 + k (direction with
+// x-component EX) to x0 + k + EX.  `q` points at column x0 of the target row;
+// `enc` turns a value into its stored form.  The aligned vector at q receives
+// the values of nodes x0 - EX .. x0 + VEC - 1 - EX through a warp shuffle; the
+// one value that crosses into the neighbouring warp's columns is stored by the
+// edge lane as a scalar, and only values of nodes inside the row are written
+// (the in-place update must leave every other slot to its own writer).  All 32
+// lanes must call this together.
+template <class S, int VEC, int EX, class C, class Enc>
+__device__ __forceinline__ void push_row(S* q, int lane, int x0, int nx, const C (&v)[VEC], Enc enc) {
+    if constexpr (VEC == 1) {
+        if (x0 < nx) q[EX] = enc(v[0]);
+        return;
+    }
+    C w[VEC];
+    if constexpr (EX == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) w[k] = v[k];
+    } else if constexpr (EX == 1) {
+        w[0] = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
+#pragma unroll
+        for (int k = 1; k < VEC; ++k) w[k] = v[k - 1];
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC - 1; ++k) w[k] = v[k + 1];
+        w[VEC - 1] = __shfl_down_sync(0xffffffffu, v[0], 1);
+    }
+    if (x0 >= nx) return;
+    // every source node x0 + k - EX inside the row and held by this warp
+    const bool whole = EX == 0 ? x0 + VEC <= nx : (EX == 1 ? (lane != 0 && x0 + VEC - 1 <= nx) : (lane != 31 && x0 + VEC < nx));
+    if (whole) {
+        S t[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) t[k] = enc(w[k]);
+        st_vec<S, VEC>(q, t);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            const int src = x0 + k - EX;
+            const bool held = !(EX == 1 && k == 0 && lane == 0) && !(EX == -1 && k == VEC - 1 && lane == 31);
+            if (held && src >= 0 && src < nx) q[k] = enc(w[k]);
+        }
+    }
+    if constexpr (EX == 1) {
+        if (lane == 31 && x0 + VEC - 1 < nx) q[VEC] = enc(v[VEC - 1]);
+    } else if constexpr (EX == -1) {
+        if (lane == 0) q[-1] = enc(v[0]);
+    }
+}
+
+// One half of an in-place step pair for the block at (bx, by, bz): MODE =
+// AA_EVEN reads every node's own slots and writes the post-collision values back
+// into the slots of the opposite directions; MODE = AA_ODD reads f_i from
+// (x - e_i) of plane ibar and pushes f+_i to (x + e_i) of plane i.  The
+// collision is the one of step_block; the wall rules go where the next half
+// reads them (ghost_write).  One buffer: `buf` is read and written.
+template <int DIM, class S, int VEC, bool TRT, int MODE>
+__device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, int by, int bz) {
+    using LF = typename Lat<DIM>::F;
+    using LG = typename Lat<DIM>::G;
+    using C = typename Storage<S>::C;
+    constexpr int QF = LF::Q, QG = LG::Q;
+    const Layout& L = p.L;
+    const int lane = threadIdx.x & 31;
+    const int y = by * blockDim.y + threadIdx.y;
+    const int z = DIM == 3 ? bz : 0;
+    if (y >= L.ny) return;  // uniform across the warp
+    const int x0 = (bx * blockDim.x + threadIdx.x) * VEC;
+    if (x0 - lane * VEC >= L.nx) return;  // the whole warp lies past the row end
+    const int x0ld = min(x0, p.xmax_load);
+    const C scale = ScaleOf<C>::s(p);
+    const C inv_scale = ScaleOf<C>::inv(p);
+    const long long row = L.row(y, z);
+    constexpr bool KS = TRT && Storage<S>::offset;
+
+    C f[QF][VEC], g[QG][VEC];
+    const S* own_ld = buf + row + x0ld;
+    static_for<QF>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        C t[VEC];
+        if constexpr (MODE == AA_EVEN) pull_row<S, VEC, 0, C>(own_ld + p.soff[i], lane, t);
+        else pull_row<S, VEC, LF::e(i, 0), C>(own_ld + p.oload[i], lane, t);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) f[i][k] = raw_to_dev_k<LF, S, C, KS>(t[k], i, inv_scale);
+    });
+    static_for<QG>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        C t[VEC];
+        if constexpr (MODE == AA_EVEN) pull_row<S, VEC, 0, C>(own_ld + p.soff[QF + i], lane, t);
+        else pull_row<S, VEC, LG::e(i, 0), C>(own_ld + p.oload[QF + i], lane, t);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g_k<S, C, KS>(t[k], inv_scale);
+    });
+
+    collide_vec<DIM, TRT, C, KS, VEC>(f, g, p);
+
+    S* own = buf + row + x0;
+    if constexpr (MODE == AA_EVEN) {
+        if (x0 >= L.nx) return;
+        // own slots, opposite planes
+        if (x0 + VEC <= L.nx) {
+            static_for<QF>([&](auto ii) {
+                constexpr int i = decltype(ii)::value;
+                S v[VEC];
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                st_vec<S, VEC>(own + p.soff[LF::opp(i)], v);
+            });
+            static_for<QG>([&](auto ii) {
+                constexpr int i = decltype(ii)::value;
+                S v[VEC];
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
+                st_vec<S, VEC>(own + p.soff[QF + LG::opp(i)], v);
+            });
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                if (x0 + k < L.nx) {
+                    static_for<QF>([&](auto ii) {
+                        constexpr int i = decltype(ii)::value;
+                        own[p.soff[LF::opp(i)] + k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                    });
+                    static_for<QG>([&](auto ii) {
+                        constexpr int i = decltype(ii)::value;
+                        own[p.soff[QF + LG::opp(i)] + k] = enc_g_k<S, C, KS>(g[i][k], scale);
+                    });
+                }
+            }
+        }
+    } else {
+        // push to x + e_i of plane i (all lanes take part in the shuffles)
+        static_for<QF>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            push_row<S, VEC, LF::e(i, 0), C>(own + p.ostore[i], lane, x0, L.nx, f[i],
+                                             [&](C d) { return enc_f_k<LF, S, C, KS>(d, i, scale); });
+        });
+        static_for<QG>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            push_row<S, VEC, LG::e(i, 0), C>(own + p.ostore[QF + i], lane, x0, L.nx, g[i],
+                                             [&](C d) { return enc_g_k<S, C, KS>(d, scale); });
+        });
+        if (x0 >= L.nx) return;
+    }
+    wall_writes<DIM, S, VEC, C, KS, MODE>(buf, p, x0, y, z, f, g);
+}
+
+template <int DIM, class S, int VEC, bool TRT, int MODE>
+__global__ void step_kernel_aa(S* buf, const KParams p) {
+    step_block_aa<DIM, S, VEC, TRT, MODE>(buf, p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ------------------------------------------------------------------ software-pipelined rows
@@ -1108,7 +1296,18 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
 
 // ------------------------------------------------------------------ diagnostics
 
-// Canonical pre-collision populations of one node (scalar pulls).
+// Element index (within the planes of set LS) of the pre-collision value
+// f_j(x) of the state, in the order p.state names.
+template <class LS, int j>
+__device__ __forceinline__ long long pre_index(const KParams& p, int x, int y, int z) {
+    const Layout& L = p.L;
+    constexpr int ex = LS::e(j, 0), ey = LS::e(j, 1), ez = LS::e(j, 2);
+    if (p.state == 1) return (long long)j * L.plane + L.slot(x, y, z);
+    const int plane = p.state == 2 ? LS::opp(j) : j;
+    return (long long)plane * L.plane + L.slot(x - ex, y - ey, z - ez);
+}
+
+// Canonical pre-collision populations of one node (scalar reads).
 template <int DIM, class S, class C>
 __device__ __forceinline__ void pull_node(const S* __restrict__ src, const KParams& p, int x, int y, int z,
                                           C (&f)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q]) {
@@ -1119,12 +1318,12 @@ __device__ __forceinline__ void pull_node(const S* __restrict__ src, const KPara
     const S* __restrict__ gsrc = src + (long long)LF::Q * L.plane;
     static_for<LF::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        const C raw = to_c<C>(src[(long long)i * L.plane + L.slot(x - LF::e(i, 0), y - LF::e(i, 1), z - LF::e(i, 2))]);
+        const C raw = to_c<C>(src[pre_index<LF, i>(p, x, y, z)]);
         f[i] = raw_to_dev<LF, S, C>(raw, i, inv_scale);
     });
     static_for<LG::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        const C raw = to_c<C>(gsrc[(long long)i * L.plane + L.slot(x - LG::e(i, 0), y - LG::e(i, 1), z - LG::e(i, 2))]);
+        const C raw = to_c<C>(gsrc[pre_index<LG, i>(p, x, y, z)]);
         g[i] = raw_to_g<S, C>(raw, inv_scale);
     });
 }

@@ -13,6 +13,9 @@ cudaError_t launch_step_2d_f16(int prec, int vec, bool trt, int rows, const void
         TLBM_ROWS_CASE(2, __half, 4, 4)
         TLBM_ROWS_CASE(2, __half, 8, 2)
         TLBM_ROWS_CASE(2, __half, 8, 4)
+        TLBM_AA_CASE(2, __half, 4, true)
+        TLBM_AA_CASE(2, __half, 1, true)
+        TLBM_AA_CASE(2, __half, 4, false)
     } else {
         TLBM_STEP_CASE(2, __nv_bfloat16, 8, true)
         TLBM_STEP_CASE(2, __nv_bfloat16, 4, true)
@@ -22,6 +25,9 @@ cudaError_t launch_step_2d_f16(int prec, int vec, bool trt, int rows, const void
         TLBM_ROWS_CASE(2, __nv_bfloat16, 4, 4)
         TLBM_ROWS_CASE(2, __nv_bfloat16, 8, 2)
         TLBM_ROWS_CASE(2, __nv_bfloat16, 8, 4)
+        TLBM_AA_CASE(2, __nv_bfloat16, 4, true)
+        TLBM_AA_CASE(2, __nv_bfloat16, 1, true)
+        TLBM_AA_CASE(2, __nv_bfloat16, 4, false)
     }
     return cudaErrorInvalidValue;
 }
@@ -36,6 +42,9 @@ const void* func_step_2d_f16(int prec, int vec, bool trt, int rows) {
         TLBM_ROWS_FUNC(2, __half, 4, 4)
         TLBM_ROWS_FUNC(2, __half, 8, 2)
         TLBM_ROWS_FUNC(2, __half, 8, 4)
+        TLBM_AA_FUNC(2, __half, 4, true)
+        TLBM_AA_FUNC(2, __half, 1, true)
+        TLBM_AA_FUNC(2, __half, 4, false)
     } else {
         TLBM_STEP_FUNC(2, __nv_bfloat16, 8, true)
         TLBM_STEP_FUNC(2, __nv_bfloat16, 4, true)
@@ -45,6 +54,9 @@ const void* func_step_2d_f16(int prec, int vec, bool trt, int rows) {
         TLBM_ROWS_FUNC(2, __nv_bfloat16, 4, 4)
         TLBM_ROWS_FUNC(2, __nv_bfloat16, 8, 2)
         TLBM_ROWS_FUNC(2, __nv_bfloat16, 8, 4)
+        TLBM_AA_FUNC(2, __nv_bfloat16, 4, true)
+        TLBM_AA_FUNC(2, __nv_bfloat16, 1, true)
+        TLBM_AA_FUNC(2, __nv_bfloat16, 4, false)
     }
     return nullptr;
 }

@@ -10,6 +10,9 @@ cudaError_t launch_step_2d_f32(int vec, bool trt, int rows, const void* src, voi
     TLBM_STEP_CASE(2, float, 4, false)
     TLBM_ROWS_CASE(2, float, 4, 2)
     TLBM_ROWS_CASE(2, float, 4, 4)
+    TLBM_AA_CASE(2, float, 4, true)
+    TLBM_AA_CASE(2, float, 1, true)
+    TLBM_AA_CASE(2, float, 4, false)
     return cudaErrorInvalidValue;
 }
 
@@ -20,6 +23,9 @@ const void* func_step_2d_f32(int vec, bool trt, int rows) {
     TLBM_STEP_FUNC(2, float, 4, false)
     TLBM_ROWS_FUNC(2, float, 4, 2)
     TLBM_ROWS_FUNC(2, float, 4, 4)
+    TLBM_AA_FUNC(2, float, 4, true)
+    TLBM_AA_FUNC(2, float, 1, true)
+    TLBM_AA_FUNC(2, float, 4, false)
     return nullptr;
 }
 }  // namespace tlbm

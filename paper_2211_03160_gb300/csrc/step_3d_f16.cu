@@ -11,6 +11,9 @@ cudaError_t launch_step_3d_f16(int prec, int vec, bool trt, int rows, const void
         TLBM_STEP_CASE(3, __half, 4, false)
         TLBM_ROWS_CASE(3, __half, 1, 2)
         TLBM_ROWS_CASE(3, __half, 1, 4)
+        TLBM_AA_CASE(3, __half, 2, true)
+        TLBM_AA_CASE(3, __half, 1, true)
+        TLBM_AA_CASE(3, __half, 2, false)
     } else {
         TLBM_STEP_CASE(3, __nv_bfloat16, 4, true)
         TLBM_STEP_CASE(3, __nv_bfloat16, 2, true)
@@ -18,6 +21,9 @@ cudaError_t launch_step_3d_f16(int prec, int vec, bool trt, int rows, const void
         TLBM_STEP_CASE(3, __nv_bfloat16, 4, false)
         TLBM_ROWS_CASE(3, __nv_bfloat16, 1, 2)
         TLBM_ROWS_CASE(3, __nv_bfloat16, 1, 4)
+        TLBM_AA_CASE(3, __nv_bfloat16, 2, true)
+        TLBM_AA_CASE(3, __nv_bfloat16, 1, true)
+        TLBM_AA_CASE(3, __nv_bfloat16, 2, false)
     }
     return cudaErrorInvalidValue;
 }
@@ -30,6 +36,9 @@ const void* func_step_3d_f16(int prec, int vec, bool trt, int rows) {
         TLBM_STEP_FUNC(3, __half, 4, false)
         TLBM_ROWS_FUNC(3, __half, 1, 2)
         TLBM_ROWS_FUNC(3, __half, 1, 4)
+        TLBM_AA_FUNC(3, __half, 2, true)
+        TLBM_AA_FUNC(3, __half, 1, true)
+        TLBM_AA_FUNC(3, __half, 2, false)
     } else {
         TLBM_STEP_FUNC(3, __nv_bfloat16, 4, true)
         TLBM_STEP_FUNC(3, __nv_bfloat16, 2, true)
@@ -37,6 +46,9 @@ const void* func_step_3d_f16(int prec, int vec, bool trt, int rows) {
         TLBM_STEP_FUNC(3, __nv_bfloat16, 4, false)
         TLBM_ROWS_FUNC(3, __nv_bfloat16, 1, 2)
         TLBM_ROWS_FUNC(3, __nv_bfloat16, 1, 4)
+        TLBM_AA_FUNC(3, __nv_bfloat16, 2, true)
+        TLBM_AA_FUNC(3, __nv_bfloat16, 1, true)
+        TLBM_AA_FUNC(3, __nv_bfloat16, 2, false)
     }
     return nullptr;
 }

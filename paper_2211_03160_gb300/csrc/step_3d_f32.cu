@@ -10,6 +10,9 @@ cudaError_t launch_step_3d_f32(int vec, bool trt, int rows, const void* src, voi
     TLBM_STEP_CASE(3, float, 2, false)
     TLBM_ROWS_CASE(3, float, 1, 2)
     TLBM_ROWS_CASE(3, float, 1, 4)
+    TLBM_AA_CASE(3, float, 1, true)
+    TLBM_AA_CASE(3, float, 2, true)
+    TLBM_AA_CASE(3, float, 1, false)
     return cudaErrorInvalidValue;
 }
 
@@ -20,6 +23,9 @@ const void* func_step_3d_f32(int vec, bool trt, int rows) {
     TLBM_STEP_FUNC(3, float, 2, false)
     TLBM_ROWS_FUNC(3, float, 1, 2)
     TLBM_ROWS_FUNC(3, float, 1, 4)
+    TLBM_AA_FUNC(3, float, 1, true)
+    TLBM_AA_FUNC(3, float, 2, true)
+    TLBM_AA_FUNC(3, float, 1, false)
     return nullptr;
 }
 }  // namespace tlbm

@@ -10,10 +10,14 @@ cudaError_t launch_step_f64(int dim, int vec, bool trt, int rows, const void* sr
         TLBM_STEP_CASE(2, double, 2, true)
         TLBM_STEP_CASE(2, double, 1, true)
         TLBM_STEP_CASE(2, double, 2, false)
+        TLBM_AA_CASE(2, double, 2, true)
+        TLBM_AA_CASE(2, double, 2, false)
     } else {
         TLBM_STEP_CASE(3, double, 1, true)
         TLBM_STEP_CASE(3, double, 2, true)
         TLBM_STEP_CASE(3, double, 1, false)
+        TLBM_AA_CASE(3, double, 1, true)
+        TLBM_AA_CASE(3, double, 1, false)
     }
     return cudaErrorInvalidValue;
 }
@@ -23,10 +27,14 @@ const void* func_step_f64(int dim, int vec, bool trt, int rows) {
         TLBM_STEP_FUNC(2, double, 2, true)
         TLBM_STEP_FUNC(2, double, 1, true)
         TLBM_STEP_FUNC(2, double, 2, false)
+        TLBM_AA_FUNC(2, double, 2, true)
+        TLBM_AA_FUNC(2, double, 2, false)
     } else {
         TLBM_STEP_FUNC(3, double, 1, true)
         TLBM_STEP_FUNC(3, double, 2, true)
         TLBM_STEP_FUNC(3, double, 1, false)
+        TLBM_AA_FUNC(3, double, 1, true)
+        TLBM_AA_FUNC(3, double, 1, false)
     }
     return nullptr;
 }

@@ -28,6 +28,7 @@ TLBM_D3Q19_D3Q7 = 1
 TLBM_FP64, TLBM_FP32, TLBM_FP16_OFFSET, TLBM_BF16_OFFSET = 0, 1, 2, 3
 TLBM_RB, TLBM_SIDE_HEATED = 0, 1
 TLBM_OUT_F64, TLBM_OUT_F32 = 0, 1
+TLBM_STREAM_PULL, TLBM_STREAM_INPLACE = 0, 1
 
 PRECISIONS = {"fp64": TLBM_FP64, "fp32": TLBM_FP32, "fp16": TLBM_FP16_OFFSET, "bf16": TLBM_BF16_OFFSET}
 
@@ -40,7 +41,7 @@ class tlbm_params(C.Structure):
         ("s_q", C.c_double), ("s_pi", C.c_double), ("s_m", C.c_double),
         ("q_e", C.c_double), ("q_v", C.c_double),
         ("body_force", C.c_double * 3), ("Th", C.c_double), ("Tc", C.c_double),
-        ("store_scale", C.c_double),
+        ("store_scale", C.c_double), ("streaming", C.c_int),
     ]
 
 

@@ -157,3 +157,20 @@ def test_binding_argument_counts_match_the_header(T):
                 depth -= ch in ")]}"
                 count += ch == "," and depth == 0
             assert count == n, (name, count, n)
+
+
+def test_inplace_streaming_needs_one_buffer(T):
+    p = T.tlbm_default_params()
+    assert p.streaming == T.TLBM_STREAM_PULL
+    h2 = T.tlbm_create(8193, 8193, 1, 0, 1e8, 0.71, 0.1, 1, p)
+    h1 = T.tlbm_create(8193, 8193, 1, 0, 1e8, 0.71, 0.1, 1, T.tlbm_default_params(streaming=T.TLBM_STREAM_INPLACE))
+    try:
+        b2, b1 = T.tlbm_required_bytes(h2), T.tlbm_required_bytes(h1)
+        pop = 14 * 4 * 8193 * 8193
+        assert pop <= b2 - b1 < 1.2 * pop
+    finally:
+        T.tlbm_destroy(h2)
+        T.tlbm_destroy(h1)
+    with pytest.raises(T.TlbmError) as ei:
+        T.tlbm_create(10, 10, 1, 0, 1e5, 0.71, 0.1, 1, T.tlbm_default_params(streaming=2))
+    assert ei.value.code == T.TLBM_ERR_ARG
