@@ -174,7 +174,11 @@ def max_over_ranks(v: float, ws: int, device=None) -> float:
 # ------------------------------------------------------------------ workloads
 
 def workload(name: str):
-    """(dim, nx, ny, nz, Ra, precision name, seed) of a named workload."""
+    """(dim, nx, ny, nz, Ra, precision name, seed) of a named workload; a name
+    ending in "_inplace" is the same workload with in-place streaming, one
+    ending in "_side" the paper's side-heated cavity instead of the
+    Rayleigh-Benard cell."""
+    name = name.removesuffix("_inplace").removesuffix("_side")
     table = {
         "2d_8193_fp32": (2, 8193, 8193, 1, 1e8, "fp32", 2),
         "2d_8193_fp16": (2, 8193, 8193, 1, 1e8, "fp16", 2),
@@ -191,13 +195,25 @@ def workload(name: str):
     return table[name]
 
 
+def inplace(name: str) -> bool:
+    return name.endswith("_inplace")
+
+
+def side_heated(name: str) -> bool:
+    return name.endswith("_side")
+
+
 def describe(name: str) -> str:
     dim, nx, ny, nz, Ra, prec, seed = workload(name)
+    how = ", in-place (AA) streaming in one buffer" if inplace(name) else ""
+    if side_heated(name):
+        return (f"2D side-heated cavity D2Q9+D2Q5 {nx}x{ny}, {prec.upper()} storage, Ra={Ra:g}, Pr=0.71, Ma=0.1, "
+                f"seed {seed}, noise 1e-3")
     if dim == 2:
         return (f"2D Rayleigh-Benard D2Q9+D2Q5 {nx}x{ny}, {prec.upper()} storage, Ra={Ra:g}, Pr=0.71, Ma=0.1, "
-                f"seed {seed}, noise 1e-3")
+                f"seed {seed}, noise 1e-3{how}")
     return (f"3D Rayleigh-Benard cube D3Q19+D3Q7 {nx}x{ny}x{nz}, {prec.upper()} storage, Ra={Ra:g}, Pr=0.71, "
-            f"Ma=0.1, seed {seed}, noise 1e-3")
+            f"Ma=0.1, seed {seed}, noise 1e-3{how}")
 
 
 def run_gpu(name: str, steps: int, warmup: int, ws: int, device_index: int, e2e: bool):
@@ -211,7 +227,9 @@ def run_gpu(name: str, steps: int, warmup: int, ws: int, device_index: int, e2e:
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = tlbm.Sim(nx, ny, nz, lattice=lattice, Ra=Ra, Pr=0.71, Ma=0.1, precision=tlbm.PRECISIONS[prec],
-                       stream=stream)
+                       stream=stream,
+                       streaming=tlbm.TLBM_STREAM_INPLACE if inplace(name) else tlbm.TLBM_STREAM_PULL,
+                       walls=tlbm.TLBM_SIDE_HEATED if side_heated(name) else tlbm.TLBM_RB)
         sim.init(seed, 1e-3)
         sim.step(warmup)
         stream.synchronize()
@@ -233,6 +251,7 @@ def run_gpu(name: str, steps: int, warmup: int, ws: int, device_index: int, e2e:
         out = {
             "name": name, "nodes": nodes, "dim": dim, "prec": prec, "sec": sec, "sec_max": sec_max,
             "glups_rank": nodes * steps / sec / 1e9, "launches": launches, "clocks": clk.summary(),
+            "device_bytes": sim.nbytes,
         }
         div, _ = sim.status()
         out["diverged"] = bool(div)
@@ -398,6 +417,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d_8193_fp32")
     ap.add_argument("--variants", default="2d_8193_fp16,2d_8193_bf16,3d_385_fp32,3d_385_fp16,2d_8193_fp64,"
+                                          "2d_8193_fp32_inplace,3d_385_fp16_inplace,2d_8193_fp32_side,"
                                           "batch64_fp32,batch64_fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -446,7 +466,7 @@ def main():
                        "unit": "GLUPS", "ms_per_step": r["sec_max"] / st * 1e3,
                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                     "frac": gbs / peaks["hbm_gbs"], "bytes_per_lu": bpl},
-                       "diverged": r["diverged"], "nusselt": r["nusselt"]}
+                       "diverged": r["diverged"], "nusselt": r["nusselt"], "device_bytes": r["device_bytes"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
