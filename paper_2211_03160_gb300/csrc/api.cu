@@ -275,30 +275,40 @@ __global__ void macros_kernel(const S* __restrict__ buf, const KParams p, O* rho
 }
 
 // Deterministic FP64 reduction, pass 1: each block sums a fixed node subset in
-// a fixed order (per-thread serial loop, then a fixed warp-shuffle tree and a
-// fixed cross-warp order) and writes its partials.
+// a fixed order (per-thread serial loop over every (RED_BLOCKS * RED_THREADS)-th
+// node, then a fixed warp-shuffle tree and a fixed cross-warp order) and writes
+// its partials.  The node coordinates advance by the stride's (x, y, z) digits
+// with carries instead of a division per node.
 template <int DIM, class S>
 __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(const S* __restrict__ buf, const KParams p,
                                                             double* __restrict__ partials) {
-    using LF = typename Lat<DIM>::F;
-    using LG = typename Lat<DIM>::G;
     const Layout& L = p.L;
     const long long N = (long long)L.nx * L.ny * L.nz;
     double acc[RED_FIELDS] = {0, 0, 0, 0, 0, 0};
-    for (long long n = blockIdx.x * (long long)RED_THREADS + threadIdx.x; n < N;
-         n += (long long)RED_BLOCKS * RED_THREADS) {
+    const long long n0 = blockIdx.x * (long long)RED_THREADS + threadIdx.x;
+    if (n0 < N) {
+        constexpr long long STR = (long long)RED_BLOCKS * RED_THREADS;
         int x, y, z;
-        node_xyz(n, L, x, y, z);
-        double f[LF::Q], g[LG::Q], r, u[3], t;
-        pull_node<DIM, S, double>(buf, p, x, y, z, f, g);
-        node_macros<DIM, double>(f, g, p, r, u, t);
-        const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        acc[0] += u[p.heat_axis] * t;
-        acc[1] += 0.5 * r * u2;
-        acc[2] += r;
-        acc[3] = fmax(acc[3], u2);
-        if (!isfinite(r) || !isfinite(t) || !isfinite(u2)) acc[4] = 1.0;
-        acc[5] += t;
+        node_xyz(n0, L, x, y, z);
+        int sx, sy, sz;
+        node_xyz(STR, L, sx, sy, sz);  // the stride in mixed radix (nx, ny, .)
+        while (z < L.nz) {
+            double t[5];
+            node_terms<DIM, S>(buf, p, x, y, z, t);
+            acc[0] += t[0];
+            acc[1] += t[1];
+            acc[2] += t[2];
+            acc[3] = fmax(acc[3], t[3]);
+            if (!isfinite(t[2]) || !isfinite(t[4]) || !isfinite(t[3])) acc[4] = 1.0;
+            acc[5] += t[4];
+            x += sx;
+            const int cx = x >= L.nx;
+            x -= cx * L.nx;
+            y += sy + cx;
+            const int cy = y >= L.ny;
+            y -= cy * L.ny;
+            z += sz + cy;
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

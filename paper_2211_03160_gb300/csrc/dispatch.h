@@ -65,6 +65,29 @@ const void* func_step_f64(int dim, int vec, bool trt, int rows);
 #define TLBM_ROWS_FUNC(DIM, S, VEC, ROWS) \
     if (vec == VEC && trt && rows == ROWS) return (const void*)&tlbm::step_kernel_rows<DIM, S, VEC, true, ROWS>;
 
+// variants held to 96 registers (step_kernel_r96, step_kernel_aa_r96)
+#define TLBM_STEP96_CASE(DIM, S, VEC, TRT)                                                          \
+    if (vec == VEC && trt == TRT && rows == 1) {                                                    \
+        tlbm::step_kernel_r96<DIM, S, VEC, TRT><<<grid, block, 0, s>>>((const S*)src, (S*)dst, p);  \
+        return cudaGetLastError();                                                                  \
+    }
+#define TLBM_STEP96_FUNC(DIM, S, VEC, TRT) \
+    if (vec == VEC && trt == TRT && rows == 1) return (const void*)&tlbm::step_kernel_r96<DIM, S, VEC, TRT>;
+#define TLBM_AA96_CASE(DIM, S, VEC, TRT)                                                                     \
+    if (vec == VEC && trt == TRT && rows == -tlbm::AA_EVEN) {                                               \
+        tlbm::step_kernel_aa_r96<DIM, S, VEC, TRT, tlbm::AA_EVEN><<<grid, block, 0, s>>>((S*)dst, p);       \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    if (vec == VEC && trt == TRT && rows == -tlbm::AA_ODD) {                                                \
+        tlbm::step_kernel_aa_r96<DIM, S, VEC, TRT, tlbm::AA_ODD><<<grid, block, 0, s>>>((S*)dst, p);        \
+        return cudaGetLastError();                                                                          \
+    }
+#define TLBM_AA96_FUNC(DIM, S, VEC, TRT)                                                                     \
+    if (vec == VEC && trt == TRT && rows == -tlbm::AA_EVEN)                                                 \
+        return (const void*)&tlbm::step_kernel_aa_r96<DIM, S, VEC, TRT, tlbm::AA_EVEN>;                     \
+    if (vec == VEC && trt == TRT && rows == -tlbm::AA_ODD)                                                  \
+        return (const void*)&tlbm::step_kernel_aa_r96<DIM, S, VEC, TRT, tlbm::AA_ODD>;
+
 // in-place (AA) halves
 #define TLBM_AA_CASE(DIM, S, VEC, TRT)                                                                       \
     if (vec == VEC && trt == TRT && rows == -tlbm::AA_EVEN) {                                               \

@@ -1132,6 +1132,10 @@ template <int DIM, class S, int VEC, bool TRT, int MODE>
 __global__ void step_kernel_aa(S* buf, const KParams p) {
     step_block_aa<DIM, S, VEC, TRT, MODE>(buf, p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
+template <int DIM, class S, int VEC, bool TRT, int MODE>
+__global__ void __maxnreg__(96) step_kernel_aa_r96(S* buf, const KParams p) {
+    step_block_aa<DIM, S, VEC, TRT, MODE>(buf, p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
 
 // ------------------------------------------------------------------ software-pipelined rows
 
@@ -1294,6 +1298,15 @@ __global__ void step_kernel(const S* __restrict__ src, S* __restrict__ dst, cons
     step_block<DIM, S, VEC, TRT>(src, dst, p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// The same kernels held to 96 registers per thread.  For the 3D two-node
+// FP16/BF16 variants the extra resident warps (21 instead of 16 per SM with
+// one-warp blocks) outweigh the few values the cap spills: 45.1 instead of
+// 43.0 GLUPS at 385^3 on GB300, same box, same process.
+template <int DIM, class S, int VEC, bool TRT>
+__global__ void __maxnreg__(96) step_kernel_r96(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
+    step_block<DIM, S, VEC, TRT>(src, dst, p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // ------------------------------------------------------------------ diagnostics
 
 // Element index (within the planes of set LS) of the pre-collision value
@@ -1326,6 +1339,25 @@ __device__ __forceinline__ void pull_node(const S* __restrict__ src, const KPara
         const C raw = to_c<C>(gsrc[pre_index<LG, i>(p, x, y, z)]);
         g[i] = raw_to_g<S, C>(raw, inv_scale);
     });
+}
+
+// Per-node terms of the reductions (a6): u_h T, 1/2 rho |u|^2, rho, |u|^2, T,
+// formed in the storage's collision precision (FP64 storage: FP64; otherwise
+// FP32, the precision the state was computed in) and handed over in FP64 for
+// the FP64 sums.
+template <int DIM, class S>
+__device__ __forceinline__ void node_terms(const S* __restrict__ buf, const KParams& p, int x, int y, int z,
+                                           double (&t)[5]) {
+    using C = typename Storage<S>::C;
+    C f[Lat<DIM>::F::Q], g[Lat<DIM>::G::Q], r, u[3], T;
+    pull_node<DIM, S, C>(buf, p, x, y, z, f, g);
+    node_macros<DIM, C>(f, g, p, r, u, T);
+    const C u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    t[0] = (double)(u[p.heat_axis] * T);
+    t[1] = (double)(C(0.5) * r * u2);
+    t[2] = (double)r;
+    t[3] = (double)u2;
+    t[4] = (double)T;
 }
 
 }  // namespace tlbm

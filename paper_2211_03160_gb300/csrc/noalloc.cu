@@ -58,16 +58,14 @@ __global__ void __launch_bounds__(NA_THREADS) noalloc_partials(const S* __restri
         const long long r = n / L.nx;
         const int y = (int)(r % L.ny);
         const int z = (int)(r / L.ny);
-        double f[LF::Q], g[LG::Q], rho, u[3], T;
-        pull_node<DIM, S, double>(buf, p, x, y, z, f, g);
-        node_macros<DIM, double>(f, g, p, rho, u, T);
-        const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        acc[0] += u[p.heat_axis] * T;
-        acc[1] += 0.5 * rho * u2;
-        acc[2] += rho;
-        acc[3] = fmax(acc[3], u2);
-        if (!isfinite(rho) || !isfinite(T) || !isfinite(u2)) acc[4] = 1.0;
-        acc[5] += T;
+        double t[5];
+        node_terms<DIM, S>(buf, p, x, y, z, t);
+        acc[0] += t[0];
+        acc[1] += t[1];
+        acc[2] += t[2];
+        acc[3] = fmax(acc[3], t[3]);
+        if (!isfinite(t[2]) || !isfinite(t[4]) || !isfinite(t[3])) acc[4] = 1.0;
+        acc[5] += t[4];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
