@@ -297,7 +297,9 @@ def ensemble_draws(n: int = 64, master_seed: int = 4):
 
 def run_batch(prec: str, steps: int, warmup: int, ws: int, device_index: int) -> dict:
     """The ensemble stepped by one flattened launch per step (CUDA-graph step
-    blocks) against the same 64 cells stepped by 64 separate launches per step."""
+    blocks) and by the persistent kernel (many steps per launch, grid barrier
+    between steps) against the same 64 cells stepped by 64 separate launches per
+    step."""
     import torch
 
     from paper_2211_03160_gb300 import tlbm
@@ -323,6 +325,19 @@ def run_batch(prec: str, steps: int, warmup: int, ws: int, device_index: int) ->
         out["batched"] = {"sec": max_over_ranks(sec, ws, torch.device("cuda", device_index) if ws > 1 else None),
                           "launches": b.launches - l0, "variant": list(b.variant),
                           "diverged": sum(b.status())}
+        # the persistent form: 64 steps per cooperative launch, grid barrier between steps
+        b.set_persistent(64)
+        b.step(warmup)
+        barrier(ws)
+        torch.cuda.synchronize()
+        l0 = b.launches
+        ev0.record(stream)
+        b.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        out["persistent"] = {"sec": max_over_ranks(sec, ws, torch.device("cuda", device_index) if ws > 1 else None),
+                             "launches": b.launches - l0, "diverged": sum(b.status())}
         b.close()
         sims = [tlbm.Sim(nx, ny, nz, lattice=tlbm.TLBM_D2Q9_D2Q5, Ra=Ra, Pr=Pr, Ma=Ma,
                          precision=tlbm.PRECISIONS[prec], stream=stream) for nx, ny, nz, Ra, Pr, Ma, _ in inst]
@@ -450,6 +465,8 @@ def main():
                              f"Pr in {{0.71,7}}, {r['prec'].upper()} storage, {r['nodes']} nodes"),
                 "steps": st, "unit": "GLUPS",
                 "value": r["nodes"] * ws * st / bt["sec"] / 1e9,
+                "persistent_value": r["nodes"] * ws * st / r["persistent"]["sec"] / 1e9,
+                "persistent_launches": r["persistent"]["launches"],
                 "separate_launches_value": r["nodes"] * ws * st / sp["sec"] / 1e9,
                 "speedup_vs_separate": sp["sec"] / bt["sec"],
                 "batched_launches": bt["launches"], "separate_launches": sp["launches"],

@@ -259,11 +259,21 @@ TLBM_API int tlbm_batch_step(tlbm_batch_t b, int64_t n);
  * tlbm_set_variant) and the steps per graph launch (even; 0 = no graph). */
 TLBM_API int tlbm_batch_set_variant(tlbm_batch_t b, int vec, int form, int block_x, int block_y,
                                     int graph_steps);
+/* Persistent form: steps_per_launch > 0 makes tlbm_batch_step run up to that
+ * many steps per launch of one cooperative kernel whose blocks (as many as fit
+ * on the device at once) work through the tiles of every instance in a fixed
+ * order and meet at a grid barrier between steps; 0 returns to one flattened
+ * launch per step (graph-captured).  The barrier's waits are bounded: a block
+ * that waits too long gives up, and tlbm_batch_status then returns
+ * TLBM_ERR_TIMEOUT.  TLBM_ERR_UNSUPPORTED without cooperative launch. */
+TLBM_API int tlbm_batch_set_persistent(tlbm_batch_t b, int steps_per_launch);
 TLBM_API int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* block_x, int* block_y,
                                     int* graph_steps);
 /* Time the compiled launch shapes (trials launches each) on the bound state and
  * keep the fastest.  The state is not changed. */
 TLBM_API int tlbm_batch_autotune(tlbm_batch_t b, int trials);
+/* (trials < 0: reuse the shape this process tuned for the same lattice, storage,
+ * collision form and size class floor(log2(total nodes)), if any.) */
 /* Borrow instance idx as a single-cell handle (owned by the batch). */
 TLBM_API int tlbm_batch_instance(tlbm_batch_t b, int idx, tlbm_t* out);
 /* Per-instance Nusselt numbers / divergence flags into nu[n] / diverged[n]. */

@@ -7,7 +7,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -28,18 +32,17 @@ struct BatchInst {
     int gx, gy;          // blocks along x and y of the instance (z: nz)
 };
 
-// Block b of the flattened grid belongs to the instance i with
+// Tile b of the flattened grid belongs to the instance i with
 // block0[i] <= b < block0[i+1]; its parameters are staged in shared memory.
-template <int DIM, class S, int VEC, bool TRT>
-__global__ void batch_step_kernel(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
-                                  int parity) {
-    __shared__ KParams sp;
-    __shared__ int si;
+// Called by all threads of a block together.  CG: the loads bypass L1 (the
+// persistent kernel reads what other blocks wrote in the previous step).
+template <int DIM, class S, int VEC, bool TRT, bool CG = false>
+__device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
+                                           int parity, long long b, KParams& sp, int& si) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nt = blockDim.x * blockDim.y;
     if (tid == 0) {
         int lo = 0, hi = n - 1;
-        const long long b = blockIdx.x;
         while (lo < hi) {
             const int mid = (lo + hi + 1) / 2;
             if (inst[mid].block0 <= b) lo = mid;
@@ -56,23 +59,124 @@ __global__ void batch_step_kernel(const KParams* __restrict__ kps, const BatchIn
     }
     __syncthreads();
     const BatchInst in = inst[i];
-    const long long local = (long long)blockIdx.x - in.block0;
+    const long long local = b - in.block0;
     const int bx = (int)(local % in.gx);
     const long long r = local / in.gx;
     const int by = (int)(r % in.gy);
     const int bz = (int)(r / in.gy);
-    step_block<DIM, S, VEC, TRT>((const S*)in.buf[parity], (S*)in.buf[parity ^ 1], sp, bx, by, bz);
+    step_block<DIM, S, VEC, TRT, CG>((const S*)in.buf[parity], (S*)in.buf[parity ^ 1], sp, bx, by, bz);
 }
+
+template <int DIM, class S, int VEC, bool TRT>
+__global__ void batch_step_kernel(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
+                                  int parity) {
+    __shared__ KParams sp;
+    __shared__ int si;
+    batch_tile<DIM, S, VEC, TRT>(kps, inst, n, parity, blockIdx.x, sp, si);
+}
+
+// ------------------------------------------------------------------ persistent form
+
+// Grid barrier of the persistent kernel: arrivals are counted, the last block
+// of a round opens the next generation.  Waits are bounded in time.
+struct GridSync {
+    unsigned count;
+    unsigned gen;
+    int status;  // 1: a block gave up waiting (TLBM_ERR_TIMEOUT)
+    int pad;
+};
+constexpr unsigned long long GRID_WAIT_NS = 500000000;  // 0.5 s
+
+__device__ __forceinline__ unsigned long long batch_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All blocks of the (co-resident, cooperatively launched) grid meet; returns
+// false in every block that gave up or found that another block gave up.
+__device__ __forceinline__ bool grid_sync(GridSync* gs, int& ok) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned* vgen = &gs->gen;
+        volatile int* vstat = &gs->status;
+        const unsigned g = *vgen;
+        __threadfence();  // this block's stores before its arrival
+        const unsigned prev = atomicAdd(&gs->count, 1u);
+        int good = 1;
+        if (prev == gridDim.x - 1) {
+            gs->count = 0;
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            const unsigned long long t0 = batch_ns();
+            while (*vgen == g) {
+                if (*vstat || batch_ns() - t0 > GRID_WAIT_NS) {
+                    atomicExch(&gs->status, 1);
+                    good = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();  // the other blocks' stores before this block reads them
+        ok = good && !*vstat;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// `steps` steps in one launch: the blocks work through the tiles of all
+// instances in a fixed order (block k takes tiles k, k + G, k + 2G, ...) and meet
+// at a grid barrier between steps.
+template <int DIM, class S, int VEC, bool TRT>
+__global__ void batch_persistent_kernel(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
+                                        long long tiles, int parity0, int steps, GridSync* gs) {
+    __shared__ KParams sp;
+    __shared__ int si;
+    __shared__ int ok;
+    for (int st = 0; st < steps; ++st) {
+        const int parity = (parity0 + st) & 1;
+        for (long long b = blockIdx.x; b < tiles; b += gridDim.x) {
+            batch_tile<DIM, S, VEC, TRT, true>(kps, inst, n, parity, b, sp, si);
+            __syncthreads();  // sp and si are reused by the next tile
+        }
+        if (st + 1 < steps && !grid_sync(gs, ok)) return;
+    }
+}
+
+// Persistent launch parameters (steps > 0 selects the persistent kernel: grid
+// = the co-resident block count, cooperative launch).
+struct Persist {
+    int steps;
+    GridSync* gs;
+    long long tiles;
+    int* per_sm_out;  // when not launching: co-resident blocks per SM of the variant
+};
 
 #define TLBM_BATCH_CASE(DIM, S, PREC, VEC, TRT)                                                      \
     if (dim == DIM && prec == PREC && vec == VEC && trt == TRT) {                                   \
+        if (pp && pp->per_sm_out)                                                                   \
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                   \
+                pp->per_sm_out, batch_persistent_kernel<DIM, S, VEC, TRT>, block.x * block.y, 0);    \
+        if (launch && pp && pp->steps > 0) {                                                        \
+            const KParams* a0 = kps;                                                                \
+            const BatchInst* a1 = inst;                                                             \
+            int a2 = n;                                                                             \
+            long long a3 = pp->tiles;                                                               \
+            int a4 = parity, a5 = pp->steps;                                                        \
+            GridSync* a6 = pp->gs;                                                                  \
+            void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};                                     \
+            return cudaLaunchCooperativeKernel((const void*)batch_persistent_kernel<DIM, S, VEC, TRT>, \
+                                               dim3((unsigned)grid), block, args, 0, s);            \
+        }                                                                                           \
         if (launch)                                                                                 \
             batch_step_kernel<DIM, S, VEC, TRT><<<grid, block, 0, s>>>(kps, inst, n, parity);       \
         return launch ? cudaGetLastError() : cudaSuccess;                                           \
     }
 
 cudaError_t batch_dispatch(bool launch, int dim, int prec, int vec, bool trt, const KParams* kps,
-                           const BatchInst* inst, int n, int parity, long long grid, dim3 block, cudaStream_t s) {
+                           const BatchInst* inst, int n, int parity, long long grid, dim3 block, cudaStream_t s,
+                           const Persist* pp = nullptr) {
     TLBM_BATCH_CASE(2, float, 1, 4, true)
     TLBM_BATCH_CASE(2, float, 1, 2, true)
     TLBM_BATCH_CASE(2, float, 1, 4, false)
@@ -112,8 +216,10 @@ struct tlbm_batch_s {
     size_t mem_bytes;
     KParams* d_kp;
     BatchInst* d_inst;
+    GridSync* d_sync;
     int vec, trt, bx, by;
     int graph_steps;
+    int persist_steps;  // > 0: persistent kernel, this many steps per launch
     long long total_blocks;
     int parity;
     int64_t t;
@@ -237,7 +343,8 @@ extern "C" int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* 
         off += align_up(need, 256);
     }
     b->tables_off = off;
-    b->total_bytes = off + align_up(sizeof(KParams) * n, 256) + align_up(sizeof(BatchInst) * n, 256);
+    b->total_bytes = off + align_up(sizeof(KParams) * n, 256) + align_up(sizeof(BatchInst) * n, 256) +
+                     align_up(sizeof(GridSync), 256);
     batch_default_variant(b);
     *out = b;
     return TLBM_OK;
@@ -264,6 +371,10 @@ extern "C" int tlbm_batch_bind_memory(tlbm_batch_t b, void* dev_ptr, size_t byte
     b->mem_bytes = bytes;
     b->d_kp = (KParams*)(b->mem + b->tables_off);
     b->d_inst = (BatchInst*)(b->mem + b->tables_off + align_up(sizeof(KParams) * b->n, 256));
+    b->d_sync = (GridSync*)(b->mem + b->tables_off + align_up(sizeof(KParams) * b->n, 256) +
+                            align_up(sizeof(BatchInst) * b->n, 256));
+    cudaError_t e = cudaMemset(b->d_sync, 0, sizeof(GridSync));
+    if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
     b->parity = 0;
     return upload_tables(b);
 }
@@ -321,10 +432,38 @@ static int build_graph(tlbm_batch_t b) {
     return TLBM_OK;
 }
 
+// One cooperative launch of the persistent kernel for k steps.
+static int launch_persistent(tlbm_batch_t b, int k) {
+    int per_sm = 0, dev = 0, sms = 0;
+    Persist q{0, nullptr, 0, &per_sm};
+    cudaError_t e = batch_dispatch(false, b->dim, b->prec, b->vec, b->trt != 0, nullptr, nullptr, 0, 0, 0,
+                                   dim3(b->bx, b->by, 1), nullptr, &q);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || per_sm < 1)
+        return bfail(b, TLBM_ERR_CUDA, "persistent kernel occupancy: %s", cudaGetErrorString(e));
+    const long long grid = std::min<long long>(b->total_blocks, (long long)per_sm * sms);
+    Persist pp{k, b->d_sync, b->total_blocks, nullptr};
+    e = cudaMemsetAsync(b->d_sync, 0, sizeof(GridSync), b->stream);
+    if (e == cudaSuccess)
+        e = batch_dispatch(true, b->dim, b->prec, b->vec, b->trt != 0, b->d_kp, b->d_inst, b->n, b->parity, grid,
+                           dim3(b->bx, b->by, 1), b->stream, &pp);
+    if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "persistent batch step: %s", cudaGetErrorString(e));
+    return TLBM_OK;
+}
+
 extern "C" int tlbm_batch_step(tlbm_batch_t b, int64_t n) {
     if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
     if (!b->mem) return bfail(b, TLBM_ERR_UNBOUND, "device memory not bound");
     if (n < 0) return bfail(b, TLBM_ERR_ARG, "n must be >= 0");
+    while (n > 0 && b->persist_steps > 0) {
+        const int k = (int)std::min<int64_t>(n, b->persist_steps);
+        const int rc = launch_persistent(b, k);
+        if (rc != TLBM_OK) return rc;
+        advance(b, k);
+        b->launches += 1;
+        n -= k;
+    }
     while (n > 0) {
         if (b->graph_steps >= 2 && b->parity == 0 && n >= b->graph_steps) {
             if (!b->graph) {
@@ -369,6 +508,19 @@ extern "C" int tlbm_batch_set_variant(tlbm_batch_t b, int vec, int form, int blo
     return TLBM_OK;
 }
 
+extern "C" int tlbm_batch_set_persistent(tlbm_batch_t b, int steps_per_launch) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (steps_per_launch < 0 || steps_per_launch > 1 << 20)
+        return bfail(b, TLBM_ERR_ARG, "steps_per_launch must be in [0, 2^20]");
+    int coop = 0, dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (steps_per_launch > 0 && (e != cudaSuccess || !coop))
+        return bfail(b, TLBM_ERR_UNSUPPORTED, "the device has no cooperative launch");
+    b->persist_steps = steps_per_launch;
+    return TLBM_OK;
+}
+
 extern "C" int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* block_x, int* block_y,
                                       int* graph_steps) {
     if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
@@ -380,12 +532,37 @@ extern "C" int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* 
     return TLBM_OK;
 }
 
+// Tuned launch shapes of this process, per (lattice, storage, collision form,
+// size class = floor(log2(total nodes))).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, std::array<int, 3>> g_tune_cache;
+
+static std::tuple<int, int, int, int> tune_key(tlbm_batch_t b) {
+    long long nodes = 0;
+    for (tlbm_t h : b->inst) nodes += (long long)h->nx * h->ny * h->nz;
+    int cls = 0;
+    while ((2LL << cls) <= nodes) ++cls;
+    return std::make_tuple(b->lattice, b->prec, b->trt, cls);
+}
+
 // Time each candidate launch shape on the bound state without changing it
 // (every trial step reads the current buffers and writes the other ones, and
-// the current buffers stay current), keep the fastest.
+// the current buffers stay current), keep the fastest.  trials < 0 reuses the
+// choice cached for the batch's (lattice, storage, form, size class) when there
+// is one.
 extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
     if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
     if (!b->mem) return bfail(b, TLBM_ERR_UNBOUND, "device memory not bound");
+    if (trials < 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(tune_key(b));
+        if (it != g_tune_cache.end()) {
+            b->vec = it->second[0];
+            b->bx = it->second[1];
+            b->by = it->second[2];
+            return upload_tables(b);
+        }
+    }
     const int reps = trials > 0 ? trials : 5;
     const int vecs[] = {8, 4, 2, 1};
     const int shapes[][2] = {{32, 1}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}};
@@ -432,6 +609,10 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
     b->vec = bv;
     b->bx = bbx;
     b->by = bby;
+    if (rc == TLBM_OK) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[tune_key(b)] = {bv, bbx, bby};
+    }
     int rc2 = upload_tables(b);
     return rc != TLBM_OK ? rc : rc2;
 }
@@ -456,6 +637,13 @@ extern "C" int tlbm_batch_nusselt(tlbm_batch_t b, double* nu) {
 extern "C" int tlbm_batch_status(tlbm_batch_t b, int* diverged) {
     if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
     if (!diverged) return bfail(b, TLBM_ERR_ARG, "diverged is NULL");
+    if (b->mem) {
+        GridSync gs{};
+        cudaError_t e = cudaMemcpyAsync(&gs, b->d_sync, sizeof(gs), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "status read: %s", cudaGetErrorString(e));
+        if (gs.status) return bfail(b, TLBM_ERR_TIMEOUT, "a persistent launch gave up waiting at a grid barrier");
+    }
     for (int i = 0; i < b->n; ++i) {
         int rc = tlbm_status(b->inst[i], &diverged[i], nullptr);
         if (rc != TLBM_OK) return bfail(b, rc, "instance %d: %s", i, tlbm_last_error(b->inst[i]));

@@ -638,21 +638,42 @@ __device__ __forceinline__ void node_macros(const C (&d)[Lat<DIM>::F::Q], const 
 
 // ------------------------------------------------------------------ vector IO
 
-template <class S, int VEC>
+// Loads of the populations: through the read-only path (ld.global.nc) when the
+// source buffer is not written during the kernel; CG: cached in L2 only
+// (ld.global.cg), for a kernel that reads, after a grid barrier, what other
+// blocks of the same launch wrote.
+template <bool CG, class T>
+__device__ __forceinline__ T ld_pop(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
+template <class S, bool CG>
+__device__ __forceinline__ S ld_one(const S* p) {
+    if constexpr (sizeof(S) == 2) {
+        const unsigned short t = ld_pop<CG>(reinterpret_cast<const unsigned short*>(p));
+        S v;
+        memcpy(&v, &t, 2);
+        return v;
+    } else {
+        return ld_pop<CG>(p);
+    }
+}
+
+template <class S, int VEC, bool CG = false>
 __device__ __forceinline__ void ld_vec(const S* __restrict__ p, S (&v)[VEC]) {
     constexpr int B = VEC * (int)sizeof(S);
     static_assert(B == 2 || B == 4 || B == 8 || B == 16, "vector width");
     if constexpr (B == 16) {
-        uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+        uint4 t = ld_pop<CG>(reinterpret_cast<const uint4*>(p));
         memcpy(v, &t, 16);
     } else if constexpr (B == 8) {
-        uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+        uint2 t = ld_pop<CG>(reinterpret_cast<const uint2*>(p));
         memcpy(v, &t, 8);
     } else if constexpr (B == 4) {
-        unsigned int t = __ldg(reinterpret_cast<const unsigned int*>(p));
+        unsigned int t = ld_pop<CG>(reinterpret_cast<const unsigned int*>(p));
         memcpy(v, &t, 4);
     } else {
-        unsigned short t = __ldg(reinterpret_cast<const unsigned short*>(p));
+        unsigned short t = ld_pop<CG>(reinterpret_cast<const unsigned short*>(p));
         memcpy(v, &t, 2);
     }
 }
@@ -685,30 +706,30 @@ __device__ __forceinline__ void st_vec(S* __restrict__ p, const S (&v)[VEC]) {
 // vector at q is loaded and shifted by one element through a warp shuffle; the
 // warp's edge lane fetches the one element beyond its vector directly.  All 32
 // lanes must call this together.
-template <class S, int VEC, int EX, class C>
+template <class S, int VEC, int EX, class C, bool CG = false>
 __device__ __forceinline__ void pull_row(const S* __restrict__ q, int lane, C (&out)[VEC]) {
     if constexpr (VEC == 1) {
         // one node per thread: a scalar load needs no alignment, fetch the
         // shifted element directly
-        out[0] = to_c<C>(q[-EX]);
+        out[0] = to_c<C>(CG ? ld_one<S, true>(q - EX) : q[-EX]);
         return;
     }
     S v[VEC];
-    ld_vec<S, VEC>(q, v);
+    ld_vec<S, VEC, CG>(q, v);
     if constexpr (EX == 0) {
 #pragma unroll
         for (int k = 0; k < VEC; ++k) out[k] = to_c<C>(v[k]);
     } else if constexpr (EX == 1) {
         // node x pulls from x - 1
         C left = __shfl_up_sync(0xffffffffu, to_c<C>(v[VEC - 1]), 1);
-        if (lane == 0) left = to_c<C>(q[-1]);
+        if (lane == 0) left = to_c<C>(CG ? ld_one<S, true>(q - 1) : q[-1]);
         out[0] = left;
 #pragma unroll
         for (int k = 1; k < VEC; ++k) out[k] = to_c<C>(v[k - 1]);
     } else {
         // node x pulls from x + 1
         C right = __shfl_down_sync(0xffffffffu, to_c<C>(v[0]), 1);
-        if (lane == 31) right = to_c<C>(q[VEC]);
+        if (lane == 31) right = to_c<C>(CG ? ld_one<S, true>(q + VEC) : q[VEC]);
 #pragma unroll
         for (int k = 0; k < VEC - 1; ++k) out[k] = to_c<C>(v[k + 1]);
         out[VEC - 1] = right;
@@ -820,7 +841,7 @@ __device__ __forceinline__ C raw_to_g(C raw, C inv_scale) {
 
 // Pull the pre-collision populations of nodes x0 .. x0+VEC-1 whose own slot in
 // plane 0 is `own`: f as deviations d_i = f_i - w_i, g as values.
-template <int DIM, class S, int VEC, class C, bool KS>
+template <int DIM, class S, int VEC, class C, bool KS, bool CG = false>
 __device__ __forceinline__ void pull_node_vec(const S* __restrict__ own, const KParams& p, int lane,
                                               C (&f)[Lat<DIM>::F::Q][VEC], C (&g)[Lat<DIM>::G::Q][VEC]) {
     using LF = typename Lat<DIM>::F;
@@ -829,14 +850,14 @@ __device__ __forceinline__ void pull_node_vec(const S* __restrict__ own, const K
     static_for<LF::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         C t[VEC];
-        pull_row<S, VEC, LF::e(i, 0), C>(own + p.loff[i], lane, t);
+        pull_row<S, VEC, LF::e(i, 0), C, CG>(own + p.loff[i], lane, t);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) f[i][k] = raw_to_dev_k<LF, S, C, KS>(t[k], i, inv_scale);
     });
     static_for<LG::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         C t[VEC];
-        pull_row<S, VEC, LG::e(i, 0), C>(own + p.loff[LF::Q + i], lane, t);
+        pull_row<S, VEC, LG::e(i, 0), C, CG>(own + p.loff[LF::Q + i], lane, t);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g_k<S, C, KS>(t[k], inv_scale);
     });
@@ -928,7 +949,7 @@ __device__ __forceinline__ void wall_writes(S* __restrict__ dst, const KParams& 
 // One thread updates VEC consecutive nodes of one row.  blockDim.x must be a
 // multiple of 32 so that a warp covers 32*VEC consecutive nodes of one row.
 // Body of the step for the block at grid position (bx, by, bz) of one cell.
-template <int DIM, class S, int VEC, bool TRT>
+template <int DIM, class S, int VEC, bool TRT, bool CG = false>
 __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restrict__ dst, const KParams& p, int bx,
                                            int by, int bz) {
     using LF = typename Lat<DIM>::F;
@@ -948,7 +969,7 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
     constexpr bool KS = TRT && Storage<S>::offset;  // TRT works on the stored, scaled values
 
     C f[QF][VEC], g[QG][VEC];
-    pull_node_vec<DIM, S, VEC, C, KS>(src + row + x0ld, p, lane, f, g);
+    pull_node_vec<DIM, S, VEC, C, KS, CG>(src + row + x0ld, p, lane, f, g);
 
     collide_vec<DIM, TRT, C, KS, VEC>(f, g, p);
 

@@ -109,6 +109,7 @@ _SIGS = {
     "tlbm_batch_set_variant": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "tlbm_batch_get_variant": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
     "tlbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
+    "tlbm_batch_set_persistent": (C.c_int, [C.c_void_p, C.c_int]),
     "tlbm_batch_instance": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "tlbm_batch_nusselt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_batch_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
@@ -529,6 +530,10 @@ def tlbm_batch_autotune(b, trials: int = 5):
     _bcheck(b, lib().tlbm_batch_autotune(b, int(trials)))
 
 
+def tlbm_batch_set_persistent(b, steps_per_launch: int):
+    _bcheck(b, lib().tlbm_batch_set_persistent(b, int(steps_per_launch)))
+
+
 def tlbm_batch_instance(b, idx: int):
     h = C.c_void_p()
     _bcheck(b, lib().tlbm_batch_instance(b, int(idx), C.byref(h)))
@@ -613,6 +618,9 @@ class Batch:
 
     def autotune(self, trials=5):
         tlbm_batch_autotune(self.b, trials)
+
+    def set_persistent(self, steps_per_launch):
+        tlbm_batch_set_persistent(self.b, steps_per_launch)
 
     def nusselt(self):
         return tlbm_batch_nusselt(self.b, self.n)

@@ -101,3 +101,45 @@ def test_batch_reductions_and_status(T):
     for k in range(5):
         assert abs(T.tlbm_nusselt(b.instance(k)) - nus[k]) == 0.0
     assert b.launches >= 10
+
+
+@pytest.mark.parametrize("lattice,prec", [(0, 1), (0, 2), (1, 3), (0, 0)])
+def test_persistent_batch_equals_flattened_launches(T, lattice, prec):
+    """The persistent form (one cooperative launch for many steps, a bounded grid
+    barrier between steps) computes exactly what the flattened per-step launches
+    compute, for step counts that end on either buffer and span several
+    launches."""
+    inst = _draws(6, (33, 65, 97), lattice=lattice)
+    ref = T.Batch(inst, lattice=lattice, precision=prec)
+    per = T.Batch(inst, lattice=lattice, precision=prec)
+    v = ref.variant
+    per.set_variant(v[0], v[1], v[2], v[3], 0)
+    per.set_persistent(7)
+    for b in (ref, per):
+        b.init(1e-3)
+    for n in (1, 9, 20):
+        ref.step(n)
+        per.step(n)
+        for k in (0, 3, 5):
+            (fa, ga), (fb, gb) = ref.get_populations(k), per.get_populations(k)
+            assert np.array_equal(fa, fb) and np.array_equal(ga, gb), (n, k)
+        assert per.status() == [False] * 6
+    # 30 steps: the first persistent launch of 7 steps, then ...: launches counted per launch
+    assert per.launches == 1 + 2 + 3
+    ref.close()
+    per.close()
+
+
+def test_autotune_cache_reuses_the_tuned_shape(T):
+    inst = _draws(5, (129, 257), seed=9)
+    a = T.Batch(inst, lattice=0, precision=1)
+    a.init(1e-3)
+    a.autotune(2)
+    tuned = a.variant[:4]
+    b = T.Batch(inst, lattice=0, precision=1)
+    b.init(1e-3)
+    l0 = b.launches
+    b.autotune(-1)  # cached: no timing launches
+    assert b.variant[:4] == tuned and b.launches == l0
+    a.close()
+    b.close()
