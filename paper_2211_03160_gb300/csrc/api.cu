@@ -613,6 +613,44 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
     }
     kp.scale = (float)scale;
     kp.inv_scale = (float)(1.0 / scale);
+    {
+        // FP32 constants of the two-relaxation-time collision (KParams::tf):
+        // the in-kernel expressions, one operation per statement, so that the
+        // host compiler forms each exactly as the kernel does
+        const float sc = kp.scale;
+        const int w0i = dim == 2 ? D2Q9::w36(0) : D3Q19::w36(0);
+        const int wai = dim == 2 ? D2Q9::w36(1) : D3Q19::w36(1);
+        const int wbi = dim == 2 ? D2Q9::w36(D2Q9::Q - 1) : D3Q19::w36(D3Q19::Q - 1);
+        const float w0 = (float)w0i / 36.0f, wa = (float)wai / 36.0f, wb = (float)wbi / 36.0f;
+        const float sp = kp.spf, sm = kp.smf, shp = kp.shpf, shm = kp.shmf, qp = kp.qpf, qm = kp.qmf;
+        auto& t = kp.tf;
+        t.m3shp = -3.0f * shp;
+        t.r1 = 4.5f * sp;
+        t.r3 = 3.0f * sm;
+        const float spm = sp + sm;        // (sp + sm) / 2 and (sm - sp) / 2 are exact halvings
+        t.c1 = 1.0f - 0.5f * spm;
+        const float dsm = sm - sp;
+        t.c2 = 0.5f * dsm;
+        t.omsp = 1.0f - sp;
+        t.w0s = w0 * sc;                  // sc is a power of two: exact
+        t.was = wa * sc;
+        t.wbs = wb * sc;
+        const float s9 = 9.0f * shp, s3 = 3.0f * shm;
+        t.f9a = s9 * t.was;
+        t.f9b = s9 * t.wbs;
+        t.f3a = s3 * t.was;
+        t.f3b = s3 * t.wbs;
+        const float wT = 0.5f * kp.omegaf;
+        const float qpm = qp + qm;
+        t.t1 = 1.0f - 0.5f * qpm;
+        const float dq = qm - qp;
+        t.t2 = 0.5f * dq;
+        t.qpwT = qp * wT;
+        t.hqm = 0.5f * qm;
+        t.omqp = 1.0f - qp;
+        const float rest = std::fma(-(float)(h->qg - 1), wT, 1.0f);
+        t.g0c = qp * rest;
+    }
 
     if ((long long)(h->qf + h->qg) * kp.L.plane + kp.L.P >= (1ll << 31)) {
         delete h;

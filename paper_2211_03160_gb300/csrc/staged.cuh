@@ -237,7 +237,7 @@ __global__ void __maxnreg__(NC == 8 ? 112 : 168)
             ph ^= 1;
         }
         if (!active) continue;
-        collide_trt_v<DIM, float2, KS>(fd, gd, p);
+        collide_trt_v<DIM, float2, KS, true>(fd, gd, p);
         S* own = dst + L.row(y, z) + x0 + xr;
         if (xr + 1 < tw) {
             static_for<QF>([&](auto ii) {
