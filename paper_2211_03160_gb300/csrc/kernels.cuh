@@ -482,8 +482,9 @@ __device__ __forceinline__ V vdot_unit(V x, V y, V z) {
 //
 // HC: take the per-launch constants from p.tf (formed on the host, bitwise the
 // same values) instead of forming them in every thread.  Measured on GB300:
-// +4 % for the staged 2D FP16 kernel, -1.2 % for the 3D FP16 kernel held to 96
-// registers, no change elsewhere.
+// +4 % for the staged 2D FP16 kernel, +1.6 % for the in-place 2D FP32 kernel;
+// -1 % to -7 % for the 3D FP16 kernels held to 96 registers and the batched
+// FP32 kernel, within 0.3 % elsewhere.
 template <int DIM, class V, bool SCALED, bool HC = false>
 __device__ __forceinline__ void collide_trt_v(V (&d)[Lat<DIM>::F::Q], V (&g)[Lat<DIM>::G::Q], const KParams& p) {
     using LF = typename Lat<DIM>::F;
@@ -582,17 +583,18 @@ __device__ __forceinline__ void collide_trt_v(V (&d)[Lat<DIM>::F::Q], V (&g)[Lat
     });
 }
 
-template <int DIM, bool TRT, class C, bool SCALED = false>
+template <int DIM, bool TRT, class C, bool SCALED = false, bool HC = false>
 __device__ __forceinline__ void collide(C (&d)[Lat<DIM>::F::Q], C (&g)[Lat<DIM>::G::Q], const KParams& p) {
-    if constexpr (TRT && std::is_same<C, float>::value) collide_trt_v<DIM, float, SCALED>(d, g, p);
+    if constexpr (TRT && std::is_same<C, float>::value) collide_trt_v<DIM, float, SCALED, HC>(d, g, p);
     else if constexpr (TRT) collide_trt<DIM, C, SCALED>(d, g, p);
     else if constexpr (DIM == 2) collide_2d<C>(d, g, p);
     else collide_3d<C>(d, g, p);
 }
 
 // Collide the nodes k = 0 .. VEC-1 of f[i][k], g[i][k]; two at a time on the
-// FP32 pair instructions where the form and the count allow.
-template <int DIM, bool TRT, class C, bool KS, int VEC>
+// FP32 pair instructions where the form and the count allow.  HC as for
+// collide_trt_v.
+template <int DIM, bool TRT, class C, bool KS, int VEC, bool HC = false>
 __device__ __forceinline__ void collide_vec(C (&f)[Lat<DIM>::F::Q][VEC], C (&g)[Lat<DIM>::G::Q][VEC],
                                             const KParams& p) {
     constexpr int QF = Lat<DIM>::F::Q, QG = Lat<DIM>::G::Q;
@@ -604,7 +606,7 @@ __device__ __forceinline__ void collide_vec(C (&f)[Lat<DIM>::F::Q][VEC], C (&g)[
             for (int i = 0; i < QF; ++i) fd[i] = make_float2(f[i][k], f[i][k + 1]);
 #pragma unroll
             for (int i = 0; i < QG; ++i) gd[i] = make_float2(g[i][k], g[i][k + 1]);
-            collide_trt_v<DIM, float2, KS>(fd, gd, p);
+            collide_trt_v<DIM, float2, KS, HC>(fd, gd, p);
 #pragma unroll
             for (int i = 0; i < QF; ++i) { f[i][k] = fd[i].x; f[i][k + 1] = fd[i].y; }
 #pragma unroll
@@ -618,7 +620,7 @@ __device__ __forceinline__ void collide_vec(C (&f)[Lat<DIM>::F::Q][VEC], C (&g)[
             for (int i = 0; i < QF; ++i) fd[i] = f[i][k];
 #pragma unroll
             for (int i = 0; i < QG; ++i) gd[i] = g[i][k];
-            collide<DIM, TRT, C, KS>(fd, gd, p);
+            collide<DIM, TRT, C, KS, HC>(fd, gd, p);
 #pragma unroll
             for (int i = 0; i < QF; ++i) f[i][k] = fd[i];
 #pragma unroll
@@ -1127,7 +1129,9 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
         for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g_k<S, C, KS>(t[k], inv_scale);
     });
 
-    collide_vec<DIM, TRT, C, KS, VEC>(f, g, p);
+    // 2D: constants formed on the host (1.6 % faster for 2D FP32 on GB300, 1 %
+    // slower for 3D FP16)
+    collide_vec<DIM, TRT, C, KS, VEC, DIM == 2>(f, g, p);
 
     S* own = buf + row + x0;
     if constexpr (MODE == AA_EVEN) {
