@@ -229,6 +229,14 @@ TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bloc
  * copies gives up; the next synchronising call then returns TLBM_ERR_TIMEOUT.
  * tlbm_set_variant switches back to the register kernels. */
 TLBM_API int tlbm_set_staged(tlbm_t h, int tile_width, int stages);
+/* How long a block of the staged kernel waits for a copy (or a free stage)
+ * before it gives up (default 0.2 s; 0 gives up at the first wait that has not
+ * completed when first tested, which makes the timeout path testable).  seconds in [0, 10], else
+ * TLBM_ERR_ARG.  A block that gives up first waits (at most 10 ms) for the
+ * copies it has in flight; the next synchronising call returns
+ * TLBM_ERR_TIMEOUT, and keeps doing so until tlbm_init, tlbm_init_fields or
+ * tlbm_set_populations replaces the state. */
+TLBM_API int tlbm_set_wait_limit(tlbm_t h, double seconds);
 /* Current variant (form reported as 1 MRT or 2 TRT; vec 0 for the staged
  * kernel).  Outputs may be NULL. */
 TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y, int* rows);
@@ -267,6 +275,12 @@ TLBM_API int tlbm_batch_set_variant(tlbm_batch_t b, int vec, int form, int block
  * that waits too long gives up, and tlbm_batch_status then returns
  * TLBM_ERR_TIMEOUT.  TLBM_ERR_UNSUPPORTED without cooperative launch. */
 TLBM_API int tlbm_batch_set_persistent(tlbm_batch_t b, int steps_per_launch);
+/* How long a block of the persistent kernel waits at the grid barrier before it
+ * gives up (default 0.5 s; 0 gives up at once unless the barrier is already
+ * open, which makes the timeout path testable).  seconds in [0, 10], else
+ * TLBM_ERR_ARG.  The timeout stays reported by tlbm_batch_status until
+ * tlbm_batch_init. */
+TLBM_API int tlbm_batch_set_wait_limit(tlbm_batch_t b, double seconds);
 TLBM_API int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* block_x, int* block_y,
                                     int* graph_steps);
 /* Time the compiled launch shapes (trials launches each) on the bound state and

@@ -580,6 +580,7 @@ extern "C" int tlbm_create(tlbm_t* out, int nx, int ny, int nz, int lattice, dou
         kp.plane32 = (int)kp.L.plane;
         kp.rp = (int)RP;
     }
+    h->wait_ns = TILE_WAIT_NS;
     h->vec = default_variant(dim, precision).vec;
     h->bx = default_variant(dim, precision).bx;
     h->by = default_variant(dim, precision).by;
@@ -768,6 +769,7 @@ static cudaError_t launch_step_raw(tlbm_t h, int parity, cudaStream_t s) {
         si.tiles = h->ny * h->nz * si.tiles_per_row;
         si.stages = h->staged_stages;
         si.status = (int*)(h->mem + h->status_off);
+        si.wait_ns = h->wait_ns;
         return launch_staged(h->dim, h->prec, h->staged_nc, src, dst, kp, si, h->staged_grid, h->staged_smem, s);
     }
     const int vec = h->vec;
@@ -1105,6 +1107,14 @@ extern "C" int tlbm_set_staged(tlbm_t h, int tile_width, int stages) {
     const int rc = set_staged(h, tile_width, stages);
     if (rc == TLBM_OK) h->variant_chosen = 1;
     return rc;
+}
+
+extern "C" int tlbm_set_wait_limit(tlbm_t h, double seconds) {
+    TLBM_CHECK_HANDLE(h);
+    if (!(seconds >= 0.0 && seconds <= 10.0)) return fail(h, TLBM_ERR_ARG, "seconds must be in [0, 10]");
+    h->wait_ns = (unsigned long long)(seconds * 1e9);
+    drop_graph(h);
+    return TLBM_OK;
 }
 
 extern "C" int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y, int* rows) {

@@ -85,7 +85,7 @@ struct GridSync {
     int status;  // 1: a block gave up waiting (TLBM_ERR_TIMEOUT)
     int pad;
 };
-constexpr unsigned long long GRID_WAIT_NS = 500000000;  // 0.5 s
+constexpr unsigned long long GRID_WAIT_NS = 500000000;  // default: 0.5 s
 
 __device__ __forceinline__ unsigned long long batch_ns() {
     unsigned long long t;
@@ -94,8 +94,9 @@ __device__ __forceinline__ unsigned long long batch_ns() {
 }
 
 // All blocks of the (co-resident, cooperatively launched) grid meet; returns
-// false in every block that gave up or found that another block gave up.
-__device__ __forceinline__ bool grid_sync(GridSync* gs, int& ok) {
+// false in every block that gave up (after wait_ns; 0: at once unless the
+// barrier is already open) or found that another block gave up.
+__device__ __forceinline__ bool grid_sync(GridSync* gs, int& ok, unsigned long long wait_ns) {
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         volatile unsigned* vgen = &gs->gen;
@@ -111,7 +112,7 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, int& ok) {
         } else {
             const unsigned long long t0 = batch_ns();
             while (*vgen == g) {
-                if (*vstat || batch_ns() - t0 > GRID_WAIT_NS) {
+                if (*vstat || batch_ns() - t0 > wait_ns || wait_ns == 0) {
                     atomicExch(&gs->status, 1);
                     good = 0;
                     break;
@@ -130,7 +131,8 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, int& ok) {
 // at a grid barrier between steps.
 template <int DIM, class S, int VEC, bool TRT>
 __global__ void batch_persistent_kernel(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
-                                        long long tiles, int parity0, int steps, GridSync* gs) {
+                                        long long tiles, int parity0, int steps, GridSync* gs,
+                                        unsigned long long wait_ns) {
     __shared__ KParams sp;
     __shared__ int si;
     __shared__ int ok;
@@ -140,7 +142,7 @@ __global__ void batch_persistent_kernel(const KParams* __restrict__ kps, const B
             batch_tile<DIM, S, VEC, TRT, true>(kps, inst, n, parity, b, sp, si);
             __syncthreads();  // sp and si are reused by the next tile
         }
-        if (st + 1 < steps && !grid_sync(gs, ok)) return;
+        if (st + 1 < steps && !grid_sync(gs, ok, wait_ns)) return;
     }
 }
 
@@ -149,6 +151,7 @@ __global__ void batch_persistent_kernel(const KParams* __restrict__ kps, const B
 struct Persist {
     int steps;
     GridSync* gs;
+    unsigned long long wait_ns;
     long long tiles;
     int* per_sm_out;  // when not launching: co-resident blocks per SM of the variant
 };
@@ -165,7 +168,8 @@ struct Persist {
             long long a3 = pp->tiles;                                                               \
             int a4 = parity, a5 = pp->steps;                                                        \
             GridSync* a6 = pp->gs;                                                                  \
-            void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};                                     \
+            unsigned long long a7 = pp->wait_ns;                                                    \
+            void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};                                \
             return cudaLaunchCooperativeKernel((const void*)batch_persistent_kernel<DIM, S, VEC, TRT>, \
                                                dim3((unsigned)grid), block, args, 0, s);            \
         }                                                                                           \
@@ -220,6 +224,7 @@ struct tlbm_batch_s {
     int vec, trt, bx, by;
     int graph_steps;
     int persist_steps;  // > 0: persistent kernel, this many steps per launch
+    unsigned long long wait_ns;  // grid-barrier wait limit of the persistent kernel
     long long total_blocks;
     int parity;
     int64_t t;
@@ -324,6 +329,7 @@ extern "C" int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* 
     b->prec = precision;
     b->dim = lattice == TLBM_D3Q19_D3Q7 ? 3 : 2;
     b->graph_steps = 16;
+    b->wait_ns = GRID_WAIT_NS;
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
         tlbm_t h = nullptr;
@@ -396,6 +402,8 @@ extern "C" int tlbm_batch_init(tlbm_batch_t b, double noise_amp) {
     }
     b->parity = 0;
     b->t = 0;
+    cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(GridSync), b->stream);
+    if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return TLBM_OK;
 }
 
@@ -435,7 +443,7 @@ static int build_graph(tlbm_batch_t b) {
 // One cooperative launch of the persistent kernel for k steps.
 static int launch_persistent(tlbm_batch_t b, int k) {
     int per_sm = 0, dev = 0, sms = 0;
-    Persist q{0, nullptr, 0, &per_sm};
+    Persist q{0, nullptr, 0, 0, &per_sm};
     cudaError_t e = batch_dispatch(false, b->dim, b->prec, b->vec, b->trt != 0, nullptr, nullptr, 0, 0, 0,
                                    dim3(b->bx, b->by, 1), nullptr, &q);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -443,8 +451,10 @@ static int launch_persistent(tlbm_batch_t b, int k) {
     if (e != cudaSuccess || per_sm < 1)
         return bfail(b, TLBM_ERR_CUDA, "persistent kernel occupancy: %s", cudaGetErrorString(e));
     const long long grid = std::min<long long>(b->total_blocks, (long long)per_sm * sms);
-    Persist pp{k, b->d_sync, b->total_blocks, nullptr};
-    e = cudaMemsetAsync(b->d_sync, 0, sizeof(GridSync), b->stream);
+    Persist pp{k, b->d_sync, b->wait_ns, b->total_blocks, nullptr};
+    // reset the barrier's counters; the status word stays set until the state
+    // is initialised again, so that a timeout is not lost to a later launch
+    e = cudaMemsetAsync(b->d_sync, 0, 2 * sizeof(unsigned), b->stream);
     if (e == cudaSuccess)
         e = batch_dispatch(true, b->dim, b->prec, b->vec, b->trt != 0, b->d_kp, b->d_inst, b->n, b->parity, grid,
                            dim3(b->bx, b->by, 1), b->stream, &pp);
@@ -631,6 +641,13 @@ extern "C" int tlbm_batch_nusselt(tlbm_batch_t b, double* nu) {
         int rc = tlbm_nusselt(b->inst[i], &nu[i]);
         if (rc != TLBM_OK) return bfail(b, rc, "instance %d: %s", i, tlbm_last_error(b->inst[i]));
     }
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_set_wait_limit(tlbm_batch_t b, double seconds) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!(seconds >= 0.0 && seconds <= 10.0)) return bfail(b, TLBM_ERR_ARG, "seconds must be in [0, 10]");
+    b->wait_ns = (unsigned long long)(seconds * 1e9);
     return TLBM_OK;
 }
 

@@ -24,6 +24,7 @@ struct tlbm_s {
     int staged;                // 1: shared-memory staged (TMA bulk copy) kernel
     int variant_chosen;        // set by tlbm_set_variant / tlbm_set_staged: keep the caller's choice
     int staged_tw, staged_nc, staged_stages, staged_grid;
+    unsigned long long wait_ns;  // staged kernel: give up on a copy after this long
     size_t staged_smem;
     size_t elem;               // bytes per stored value
     size_t popset_bytes;       // one population buffer (f planes then g planes)

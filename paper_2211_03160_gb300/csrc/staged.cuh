@@ -24,7 +24,7 @@
 namespace tlbm {
 
 constexpr int TILE_MAX_STAGES = 8;
-constexpr unsigned long long TILE_WAIT_NS = 200000000;  // give up on a wait after 0.2 s
+constexpr unsigned long long TILE_WAIT_NS = 200000000;  // default: give up on a wait after 0.2 s
 constexpr unsigned long long TILE_DRAIN_NS = 10000000;  // and on the drain after 10 ms
 
 struct StagedInfo {
@@ -33,6 +33,7 @@ struct StagedInfo {
     int tiles;          // ny * nz * tiles_per_row (< 2^31)
     int stages;         // tiles in flight per CTA, 2 <= stages <= TILE_MAX_STAGES
     int* status;        // device status word (0 ok, 1 timeout)
+    unsigned long long wait_ns;  // give up on a copy or a free stage after this long (0: at once)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -67,8 +68,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Wait for the phase of `parity` to complete; false after `limit_ns`.
+// Non-blocking test of the same (try_wait may suspend the thread for a while).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase of `parity` to complete; false after `limit_ns` (0: false
+// unless it has completed when first tested).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+    if (limit_ns == 0) return mbar_test_wait(bar, parity);
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
@@ -158,7 +173,7 @@ __global__ void __maxnreg__(NC == 8 ? 112 : 168)
         int i = 0;
         int s = 0, ph = 0;  // stage and the parity of its current use
         for (int t = blockIdx.x; t < si.tiles; t += G, ++i) {
-            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(ph ^ 1), TILE_WAIT_NS)) {
+            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(ph ^ 1), si.wait_ns)) {
                 if (lane == 0) atomicExch(si.status, 1);
                 break;
             }
@@ -199,7 +214,7 @@ __global__ void __maxnreg__(NC == 8 ? 112 : 168)
     const float inv_scale = ScaleOf<float>::inv(p);
     int s = 0, ph = 0;
     for (int t = blockIdx.x; t < si.tiles; t += G) {
-        if (!mbar_wait(&full[s], (uint32_t)ph, TILE_WAIT_NS)) {
+        if (!mbar_wait(&full[s], (uint32_t)ph, si.wait_ns)) {
             atomicExch(si.status, 1);
             return;
         }

@@ -81,6 +81,8 @@ _SIGS = {
     "tlbm_get_variant": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "tlbm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_double]),
+    "tlbm_batch_set_wait_limit": (C.c_int, [C.c_void_p, C.c_double]),
     "tlbm_set_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "tlbm_init_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tlbm_conv3x3_pack_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
@@ -324,6 +326,10 @@ def tlbm_set_staged(h, tile_width=0, stages=0):
     _check(h, lib().tlbm_set_staged(h, int(tile_width), int(stages)))
 
 
+def tlbm_set_wait_limit(h, seconds):
+    _check(h, lib().tlbm_set_wait_limit(h, float(seconds)))
+
+
 def tlbm_get_variant(h):
     """(vec, form, block_x, block_y, rows)"""
     v = [C.c_int() for _ in range(5)]
@@ -464,6 +470,9 @@ class Sim:
     def set_staged(self, tile_width=0, stages=0):
         tlbm_set_staged(self.h, tile_width, stages)
 
+    def set_wait_limit(self, seconds):
+        tlbm_set_wait_limit(self.h, seconds)
+
     @property
     def variant(self):
         return tlbm_get_variant(self.h)
@@ -532,6 +541,10 @@ def tlbm_batch_autotune(b, trials: int = 5):
 
 def tlbm_batch_set_persistent(b, steps_per_launch: int):
     _bcheck(b, lib().tlbm_batch_set_persistent(b, int(steps_per_launch)))
+
+
+def tlbm_batch_set_wait_limit(b, seconds):
+    _bcheck(b, lib().tlbm_batch_set_wait_limit(b, float(seconds)))
 
 
 def tlbm_batch_instance(b, idx: int):
@@ -621,6 +634,9 @@ class Batch:
 
     def set_persistent(self, steps_per_launch):
         tlbm_batch_set_persistent(self.b, steps_per_launch)
+
+    def set_wait_limit(self, seconds):
+        tlbm_batch_set_wait_limit(self.b, seconds)
 
     def nusselt(self):
         return tlbm_batch_nusselt(self.b, self.n)

@@ -174,3 +174,25 @@ def test_inplace_streaming_needs_one_buffer(T):
     with pytest.raises(T.TlbmError) as ei:
         T.tlbm_create(10, 10, 1, 0, 1e5, 0.71, 0.1, 1, T.tlbm_default_params(streaming=2))
     assert ei.value.code == T.TLBM_ERR_ARG
+
+
+def test_wait_limits_are_validated(T):
+    h = T.tlbm_create(33, 17, 1, 0, 1e5, 0.71, 0.1, 2)
+    try:
+        T.tlbm_set_wait_limit(h, 0.0)
+        T.tlbm_set_wait_limit(h, 10.0)
+        for bad in (-1e-9, 10.5, float("nan")):
+            with pytest.raises(T.TlbmError) as ei:
+                T.tlbm_set_wait_limit(h, bad)
+            assert ei.value.code == T.TLBM_ERR_ARG
+    finally:
+        T.tlbm_destroy(h)
+    b = T.tlbm_batch_create([(33, 33, 1, 1e5, 0.71, 0.1, 1), (17, 17, 1, 1e5, 0.71, 0.1, 2)], 0, 1)
+    try:
+        T.tlbm_batch_set_wait_limit(b, 0.0)
+        for bad in (-1.0, 11.0, float("nan")):
+            with pytest.raises(T.TlbmError) as ei:
+                T.tlbm_batch_set_wait_limit(b, bad)
+            assert ei.value.code == T.TLBM_ERR_ARG
+    finally:
+        T.tlbm_batch_destroy(b)
