@@ -197,6 +197,27 @@ TLBM_API int tlbm_get_populations_window(tlbm_t h, int x0, int y0, int z0, int w
  * storage precision).  Both pointers are required.  Synchronises. */
 TLBM_API int tlbm_set_populations(tlbm_t h, const double* host_f, const double* host_g);
 
+/* Checkpoint the state to the file `path` (host I/O; synchronises): a header
+ * (magic "TLBMCKP1", format version 1, byte-order mark, lattice, nx, ny, nz,
+ * storage precision, walls, periodic axes, Ra, Pr, Ma, Th, Tc, storage scale,
+ * body force, the derived parameters of tlbm_derived, the step counter, the
+ * node count) followed by the pre-collision populations in FP64 in the layout
+ * of tlbm_get_populations (flow planes, then thermal planes, each nx*ny*nz
+ * values, x fastest), native byte order; with FP16/BF16-offset storage the
+ * flow planes hold the deviations f_i - w_i (a header flag says so), the exact
+ * FP64 image of what the storage holds.  Written in chunks through the scratch
+ * of the bound block (no full host copy).  TLBM_ERR_ARG if path is NULL or
+ * cannot be written. */
+TLBM_API int tlbm_save(tlbm_t h, const char* path);
+/* Restore a file written by tlbm_save into a handle created with the same
+ * lattice, size, storage precision and physical parameters (TLBM_ERR_ARG
+ * otherwise, and for a file that is not a checkpoint or is shorter or longer
+ * than its header says); the step counter is restored too.  The file holds
+ * every stored value exactly, so stepping on after tlbm_load gives bitwise the
+ * states of the uninterrupted run.  The streaming scheme of the handle may
+ * differ from the saving one's.  Synchronises. */
+TLBM_API int tlbm_load(tlbm_t h, const char* path);
+
 /* *diverged = 1 if the state holds a non-finite value or |u| > 0.5; *step =
  * current time step.  Runs a reduction; synchronises.  Either output may be NULL. */
 TLBM_API int tlbm_status(tlbm_t h, int* diverged, int64_t* step);

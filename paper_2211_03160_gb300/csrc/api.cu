@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -185,9 +186,11 @@ __global__ void init_fields_kernel(S* __restrict__ buf, const KParams p, const f
 }
 
 // Host FP64 populations (one plane, nodes [n0, n0 + cnt)) -> the state's slots.
+// dev: offset storage takes flow values as deviations f_i - w_i (the exact
+// FP64 image of what it stores; checkpoints), otherwise as f_i.
 template <int DIM, class S>
 __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ stage, int pop, long long n0,
-                               long long cnt, const Window w, const KParams p) {
+                               long long cnt, const Window w, const KParams p, bool dev) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
     using C = typename Storage<S>::C;
@@ -201,7 +204,7 @@ __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ s
             constexpr int i = decltype(ii)::value;
             if (pop == i) {
                 S s;
-                if constexpr (Storage<S>::offset) s = from_c<S>((C)((v - LF::w36(i) / 36.0) * p.scale));
+                if constexpr (Storage<S>::offset) s = from_c<S>((C)((dev ? v : v - LF::w36(i) / 36.0) * p.scale));
                 else s = (S)v;
                 buf[pre_index<LF, i>(p, x, y, z)] = s;
             }
@@ -219,9 +222,10 @@ __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ s
 }
 
 // The state's slots -> canonical FP64 populations (one plane, nodes [n0, n0 + cnt)).
+// dev: offset storage hands out flow deviations f_i - w_i (exact) instead.
 template <int DIM, class S>
 __global__ void gather_kernel(const S* __restrict__ buf, double* __restrict__ stage, int pop, long long n0,
-                              long long cnt, const Window w, const KParams p) {
+                              long long cnt, const Window w, const KParams p, bool dev) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
     const Layout& L = p.L;
@@ -235,7 +239,7 @@ __global__ void gather_kernel(const S* __restrict__ buf, double* __restrict__ st
             if (pop == i) {
                 const double raw = to_c<double>(
                     buf[pre_index<LF, i>(p, x, y, z)]);
-                if constexpr (Storage<S>::offset) v = LF::w36(i) / 36.0 + raw * (double)p.inv_scale;
+                if constexpr (Storage<S>::offset) v = (dev ? 0.0 : LF::w36(i) / 36.0) + raw * (double)p.inv_scale;
                 else v = raw;
             }
         });
@@ -363,13 +367,13 @@ struct DiagKernels {
         return cudaGetLastError();
     }
     static cudaError_t scatter(void* buf, const double* st, int pop, long long n0, long long cnt, const Window& w,
-                               const KParams& p, cudaStream_t s) {
-        scatter_kernel<DIM, S><<<1024, 256, 0, s>>>((S*)buf, st, pop, n0, cnt, w, p);
+                               const KParams& p, cudaStream_t s, bool dev = false) {
+        scatter_kernel<DIM, S><<<1024, 256, 0, s>>>((S*)buf, st, pop, n0, cnt, w, p, dev);
         return cudaGetLastError();
     }
     static cudaError_t gather(const void* buf, double* st, int pop, long long n0, long long cnt, const Window& w,
-                              const KParams& p, cudaStream_t s) {
-        gather_kernel<DIM, S><<<1024, 256, 0, s>>>((const S*)buf, st, pop, n0, cnt, w, p);
+                              const KParams& p, cudaStream_t s, bool dev = false) {
+        gather_kernel<DIM, S><<<1024, 256, 0, s>>>((const S*)buf, st, pop, n0, cnt, w, p, dev);
         return cudaGetLastError();
     }
     static cudaError_t macros(const void* buf, const KParams& p, void* r, void* ux, void* uy, void* uz, void* T,
@@ -972,10 +976,13 @@ extern "C" int tlbm_get_populations_window(tlbm_t h, int x0, int y0, int z0, int
     return get_window(h, w, host_f, host_g);
 }
 
-extern "C" int tlbm_set_populations(tlbm_t h, const double* host_f, const double* host_g) {
-    TLBM_CHECK_HANDLE(h);
-    TLBM_CHECK_BOUND(h);
-    if (!host_f || !host_g) return fail(h, TLBM_ERR_ARG, "host_f and host_g are required");
+// Replace the state by FP64 populations delivered chunk by chunk: src(pop, n0,
+// cnt, chunk) points chunk at nodes n0 .. n0 + cnt of population pop (flow
+// planes first) and returns TLBM_OK or an error code.  reuse: src hands out
+// one host buffer again and again, so each chunk's copy must finish before the
+// next call.  Synchronises.
+template <class Src>
+static int put_state(tlbm_t h, Src src, bool reuse, bool dev = false) {
     const long long N = (long long)h->nx * h->ny * h->nz;
     const Window full = {0, 0, 0, h->nx, h->ny, h->nz};
     double* stage = (double*)(h->mem + h->stage_off);
@@ -985,22 +992,160 @@ extern "C" int tlbm_set_populations(tlbm_t h, const double* host_f, const double
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     set_cur(h, 0);
     for (int pop = 0; pop < h->qf + h->qg; ++pop) {
-        const double* srcp = pop < h->qf ? host_f + (long long)pop * N : host_g + (long long)(pop - h->qf) * N;
         for (long long n0 = 0; n0 < N; n0 += STAGE_NODES) {
             const long long cnt = std::min(STAGE_NODES, N - n0);
-            e = cudaMemcpyAsync(stage, srcp + n0, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            const double* chunk = nullptr;
+            const int rc = src(pop, n0, cnt, chunk);
+            if (rc != TLBM_OK) return rc;
+            e = cudaMemcpyAsync(stage, chunk, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync H2D");
             e = with_types(h->dim, h->prec, [&](auto K) {
-                return decltype(K)::scatter(h->buf[0], stage, pop, n0, cnt, full, h->kp, h->stream);
+                return decltype(K)::scatter(h->buf[0], stage, pop, n0, cnt, full, h->kp, h->stream, dev);
             });
             if (e != cudaSuccess) return cuda_fail(h, e, "scatter kernel");
             h->launches += 1;
+            if (reuse) {
+                e = cudaStreamSynchronize(h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+            }
         }
     }
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     h->t = 0;
     return TLBM_OK;
+}
+
+extern "C" int tlbm_set_populations(tlbm_t h, const double* host_f, const double* host_g) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (!host_f || !host_g) return fail(h, TLBM_ERR_ARG, "host_f and host_g are required");
+    const long long N = (long long)h->nx * h->ny * h->nz;
+    return put_state(h, [&](int pop, long long n0, long long, const double*& chunk) {
+        chunk = (pop < h->qf ? host_f + (long long)pop * N : host_g + (long long)(pop - h->qf) * N) + n0;
+        return (int)TLBM_OK;
+    }, false);
+}
+
+// ------------------------------------------------------------------ checkpoint files
+
+namespace {
+// File header of tlbm_save: native byte order, checked by `order`.
+struct CkptHeader {
+    char magic[8];          // "TLBMCKP1"
+    uint32_t order;         // 0x01020304 as written
+    int32_t version;        // 1
+    int32_t lattice, nx, ny, nz, precision, walls, periodic_mask, nderived;
+    int32_t flow_dev;       // 1: flow planes hold f_i - w_i (offset storage), 0: f_i
+    int32_t pad;
+    double Ra, Pr, Ma, Th, Tc, scale;
+    double body[3];
+    double derived[7 + MAXQ + 7];  // tlbm_derived: U, H, nu, alpha, gbeta, a_T, omega, S, Q
+    int64_t t;              // steps taken since the initial state
+    int64_t nodes;          // nx * ny * nz
+};
+}  // namespace
+
+static void ckpt_fill(tlbm_t h, CkptHeader& c) {
+    memset(&c, 0, sizeof(c));
+    memcpy(c.magic, "TLBMCKP1", 8);
+    c.order = 0x01020304u;
+    c.version = 1;
+    c.lattice = h->lattice;
+    c.nx = h->nx;
+    c.ny = h->ny;
+    c.nz = h->nz;
+    c.precision = h->prec;
+    c.walls = h->prm.walls;
+    c.periodic_mask = h->prm.periodic_mask;
+    c.Ra = h->Ra;
+    c.Pr = h->Pr;
+    c.Ma = h->Ma;
+    c.Th = h->prm.Th;
+    c.Tc = h->prm.Tc;
+    c.scale = h->kp.scale;
+    for (int a = 0; a < 3; ++a) c.body[a] = h->prm.body_force[a];
+    int n = 0;
+    tlbm_derived(h, c.derived, 7 + MAXQ + 7, &n);
+    c.nderived = n;
+    c.flow_dev = (h->prec == TLBM_FP16_OFFSET || h->prec == TLBM_BF16_OFFSET) ? 1 : 0;
+    c.t = h->t;
+    c.nodes = (int64_t)h->nx * h->ny * h->nz;
+}
+
+extern "C" int tlbm_save(tlbm_t h, const char* path) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (!path) return fail(h, TLBM_ERR_ARG, "path is NULL");
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return fail(h, TLBM_ERR_ARG, "cannot open %s for writing", path);
+    CkptHeader c;
+    ckpt_fill(h, c);
+    int rc = TLBM_OK;
+    if (fwrite(&c, sizeof(c), 1, fp) != 1) rc = fail(h, TLBM_ERR_ARG, "write to %s failed", path);
+    const long long N = c.nodes;
+    const Window full = {0, 0, 0, h->nx, h->ny, h->nz};
+    double* stage = (double*)(h->mem + h->stage_off);
+    double* buf = rc == TLBM_OK ? (double*)malloc((size_t)std::min(STAGE_NODES, N) * sizeof(double)) : nullptr;
+    if (rc == TLBM_OK && !buf) rc = fail(h, TLBM_ERR_OOM, "host buffer");
+    for (int pop = 0; rc == TLBM_OK && pop < h->qf + h->qg; ++pop) {
+        for (long long n0 = 0; rc == TLBM_OK && n0 < N; n0 += STAGE_NODES) {
+            const long long cnt = std::min(STAGE_NODES, N - n0);
+            cudaError_t e = with_types(h->dim, h->prec, [&](auto K) {
+                return decltype(K)::gather(h->buf[h->cur], stage, pop, n0, cnt, full, h->kp, h->stream, true);
+            });
+            h->launches += 1;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(buf, stage, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) rc = cuda_fail(h, e, "checkpoint gather");
+            else if (fwrite(buf, sizeof(double), (size_t)cnt, fp) != (size_t)cnt)
+                rc = fail(h, TLBM_ERR_ARG, "write to %s failed", path);
+        }
+    }
+    free(buf);
+    if (fclose(fp) != 0 && rc == TLBM_OK) rc = fail(h, TLBM_ERR_ARG, "closing %s failed", path);
+    return rc;
+}
+
+extern "C" int tlbm_load(tlbm_t h, const char* path) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (!path) return fail(h, TLBM_ERR_ARG, "path is NULL");
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(h, TLBM_ERR_ARG, "cannot open %s", path);
+    CkptHeader c, mine;
+    ckpt_fill(h, mine);
+    int rc = TLBM_OK;
+    if (fread(&c, sizeof(c), 1, fp) != 1 || memcmp(c.magic, "TLBMCKP1", 8) != 0 || c.order != 0x01020304u ||
+        c.version != 1)
+        rc = fail(h, TLBM_ERR_ARG, "%s is not a checkpoint of this format", path);
+    else if (c.lattice != mine.lattice || c.nx != mine.nx || c.ny != mine.ny || c.nz != mine.nz ||
+             c.precision != mine.precision)
+        rc = fail(h, TLBM_ERR_ARG, "checkpoint lattice / size / storage differ from the handle's");
+    else if (c.walls != mine.walls || c.periodic_mask != mine.periodic_mask || c.nderived != mine.nderived ||
+             c.flow_dev != mine.flow_dev ||
+             memcmp(&c.Ra, &mine.Ra, offsetof(CkptHeader, t) - offsetof(CkptHeader, Ra)) != 0)
+        rc = fail(h, TLBM_ERR_ARG, "checkpoint parameters differ from the handle's");
+    const long long N = c.nodes;
+    double* buf = rc == TLBM_OK ? (double*)malloc((size_t)std::min(STAGE_NODES, N) * sizeof(double)) : nullptr;
+    if (rc == TLBM_OK && !buf) rc = fail(h, TLBM_ERR_OOM, "host buffer");
+    if (rc == TLBM_OK) {
+        rc = put_state(h, [&](int, long long, long long cnt, const double*& chunk) {
+            if (fread(buf, sizeof(double), (size_t)cnt, fp) != (size_t)cnt)
+                return fail(h, TLBM_ERR_ARG, "%s is shorter than its header says", path);
+            chunk = buf;
+            return (int)TLBM_OK;
+        }, true, true);
+        if (rc == TLBM_OK) {
+            char extra;
+            if (fread(&extra, 1, 1, fp) != 0) rc = fail(h, TLBM_ERR_ARG, "%s is longer than its header says", path);
+        }
+        if (rc == TLBM_OK) h->t = c.t;
+    }
+    free(buf);
+    fclose(fp);
+    return rc;
 }
 
 extern "C" int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int block_y, int rows) {

@@ -81,6 +81,8 @@ _SIGS = {
     "tlbm_get_variant": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "tlbm_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "tlbm_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "tlbm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_double]),
     "tlbm_batch_set_wait_limit": (C.c_int, [C.c_void_p, C.c_double]),
     "tlbm_set_graph": (C.c_int, [C.c_void_p, C.c_int]),
@@ -330,6 +332,14 @@ def tlbm_set_wait_limit(h, seconds):
     _check(h, lib().tlbm_set_wait_limit(h, float(seconds)))
 
 
+def tlbm_save(h, path):
+    _check(h, lib().tlbm_save(h, os.fsencode(path)))
+
+
+def tlbm_load(h, path):
+    _check(h, lib().tlbm_load(h, os.fsencode(path)))
+
+
 def tlbm_get_variant(h):
     """(vec, form, block_x, block_y, rows)"""
     v = [C.c_int() for _ in range(5)]
@@ -472,6 +482,12 @@ class Sim:
 
     def set_wait_limit(self, seconds):
         tlbm_set_wait_limit(self.h, seconds)
+
+    def save(self, path):
+        tlbm_save(self.h, path)
+
+    def load(self, path):
+        tlbm_load(self.h, path)
 
     @property
     def variant(self):

@@ -196,3 +196,13 @@ def test_wait_limits_are_validated(T):
             assert ei.value.code == T.TLBM_ERR_ARG
     finally:
         T.tlbm_batch_destroy(b)
+
+
+def test_checkpoint_needs_bound_memory_and_a_path(T):
+    h = T.tlbm_create(33, 17, 1, 0, 1e5, 0.71, 0.1, 1)
+    try:
+        for fn in (T.lib().tlbm_save, T.lib().tlbm_load):
+            assert fn(h, b"/nonexistent/x.ckpt") == T.TLBM_ERR_UNBOUND
+            assert fn(h, None) == T.TLBM_ERR_UNBOUND
+    finally:
+        T.tlbm_destroy(h)
