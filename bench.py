@@ -231,6 +231,7 @@ def run_gpu(name: str, steps: int, warmup: int, ws: int, device_index: int, e2e:
                        streaming=tlbm.TLBM_STREAM_INPLACE if inplace(name) else tlbm.TLBM_STREAM_PULL,
                        walls=tlbm.TLBM_SIDE_HEATED if side_heated(name) else tlbm.TLBM_RB)
         sim.init(seed, 1e-3)
+        _, mass0 = sim.energy()
         sim.step(warmup)
         stream.synchronize()
         nodes = nx * ny * nz
@@ -256,6 +257,9 @@ def run_gpu(name: str, steps: int, warmup: int, ws: int, device_index: int, e2e:
         div, _ = sim.status()
         out["diverged"] = bool(div)
         out["nusselt"] = sim.nusselt()
+        ekin, mass = sim.energy()
+        out["ekin_per_node"] = ekin / nodes
+        out["mass_drift"] = (mass - mass0) / mass0
         if e2e:
             # end to end through the public API from pinned host memory:
             # H2D of the state, `steps` steps, D2H of the reduction result
@@ -483,7 +487,8 @@ def main():
                        "unit": "GLUPS", "ms_per_step": r["sec_max"] / st * 1e3,
                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                     "frac": gbs / peaks["hbm_gbs"], "bytes_per_lu": bpl},
-                       "diverged": r["diverged"], "nusselt": r["nusselt"], "device_bytes": r["device_bytes"]}
+                       "diverged": r["diverged"], "nusselt": r["nusselt"], "ekin_per_node": r["ekin_per_node"],
+                       "mass_drift": r["mass_drift"], "device_bytes": r["device_bytes"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -520,6 +525,8 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "nusselt": r["nusselt"],
+        "ekin_per_node": r["ekin_per_node"],
+        "mass_drift": r["mass_drift"],
         "diverged": r["diverged"],
         "variants": variants,
     }
