@@ -258,6 +258,14 @@ TLBM_API int tlbm_set_staged(tlbm_t h, int tile_width, int stages);
  * TLBM_ERR_TIMEOUT, and keeps doing so until tlbm_init, tlbm_init_fields or
  * tlbm_set_populations replaces the state. */
 TLBM_API int tlbm_set_wait_limit(tlbm_t h, double seconds);
+/* Accesses that left the population buffers, counted by a library built with
+ * TLBM_DEBUG_BOUNDS (libtlbm_debug.so): there every global load and store of
+ * the step, in-place, staged, batch, transfer, initial-state and reduction
+ * kernels is checked against the handle's population buffers; an access
+ * outside them is counted and redirected into them (never trapped).  The count
+ * covers everything since tlbm_bind_memory.  Synchronises.  The release
+ * library returns TLBM_ERR_UNSUPPORTED. */
+TLBM_API int tlbm_bounds_violations(tlbm_t h, int64_t* count);
 /* Current variant (form reported as 1 MRT or 2 TRT; vec 0 for the staged
  * kernel).  Outputs may be NULL. */
 TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y, int* rows);

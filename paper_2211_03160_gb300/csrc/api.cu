@@ -128,14 +128,12 @@ __global__ void init_kernel(S* __restrict__ buf, const KParams p, uint64_t seed,
         const C scale = (C)p.scale;
         static_for<LF::Q>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            buf[pre_index<LF, i>(p, x, y, z)] =
-                enc_f<LF, S, C>(C(0), i, scale);
+            *TLBM_DBG(p, (buf + pre_index<LF, i>(p, x, y, z)), 0, 1) = enc_f<LF, S, C>(C(0), i, scale);
         });
         S* gb = buf + (long long)LF::Q * L.plane;
         static_for<LG::Q>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            gb[pre_index<LG, i>(p, x, y, z)] =
-                enc_g<S, C>((C)gq[i], scale);
+            *TLBM_DBG(p, (gb + pre_index<LG, i>(p, x, y, z)), 0, 1) = enc_g<S, C>((C)gq[i], scale);
         });
     }
 }
@@ -173,14 +171,12 @@ __global__ void init_fields_kernel(S* __restrict__ buf, const KParams p, const f
             constexpr int i = decltype(ii)::value;
             const double eu = LF::e(i, 0) * u[0] + LF::e(i, 1) * u[1] + LF::e(i, 2) * u[2];
             const double dev = (LF::w36(i) / 36.0) * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-            buf[pre_index<LF, i>(p, x, y, z)] =
-                enc_f<LF, S, C>((C)dev, i, scale);
+            *TLBM_DBG(p, (buf + pre_index<LF, i>(p, x, y, z)), 0, 1) = enc_f<LF, S, C>((C)dev, i, scale);
         });
         S* gb = buf + (long long)LF::Q * L.plane;
         static_for<LG::Q>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            gb[pre_index<LG, i>(p, x, y, z)] =
-                enc_g<S, C>((C)gq[i], scale);
+            *TLBM_DBG(p, (gb + pre_index<LG, i>(p, x, y, z)), 0, 1) = enc_g<S, C>((C)gq[i], scale);
         });
     }
 }
@@ -206,7 +202,7 @@ __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ s
                 S s;
                 if constexpr (Storage<S>::offset) s = from_c<S>((C)((dev ? v : v - LF::w36(i) / 36.0) * p.scale));
                 else s = (S)v;
-                buf[pre_index<LF, i>(p, x, y, z)] = s;
+                *TLBM_DBG(p, (buf + pre_index<LF, i>(p, x, y, z)), 0, 1) = s;
             }
         });
         static_for<LG::Q>([&](auto ii) {
@@ -215,7 +211,7 @@ __global__ void scatter_kernel(S* __restrict__ buf, const double* __restrict__ s
                 S s;
                 if constexpr (Storage<S>::offset) s = from_c<S>((C)(v * p.scale));
                 else s = (S)v;
-                buf[(long long)LF::Q * L.plane + pre_index<LG, i>(p, x, y, z)] = s;
+                *TLBM_DBG(p, (buf + ((long long)LF::Q * L.plane + pre_index<LG, i>(p, x, y, z))), 0, 1) = s;
             }
         });
     }
@@ -237,8 +233,7 @@ __global__ void gather_kernel(const S* __restrict__ buf, double* __restrict__ st
         static_for<LF::Q>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             if (pop == i) {
-                const double raw = to_c<double>(
-                    buf[pre_index<LF, i>(p, x, y, z)]);
+                const double raw = to_c<double>(*TLBM_DBG(p, (buf + pre_index<LF, i>(p, x, y, z)), 0, 1));
                 if constexpr (Storage<S>::offset) v = (dev ? 0.0 : LF::w36(i) / 36.0) + raw * (double)p.inv_scale;
                 else v = raw;
             }
@@ -246,8 +241,8 @@ __global__ void gather_kernel(const S* __restrict__ buf, double* __restrict__ st
         static_for<LG::Q>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             if (pop == LF::Q + i) {
-                const double raw = to_c<double>(
-                    buf[(long long)LF::Q * L.plane + pre_index<LG, i>(p, x, y, z)]);
+                const double raw =
+                    to_c<double>(*TLBM_DBG(p, (buf + ((long long)LF::Q * L.plane + pre_index<LG, i>(p, x, y, z))), 0, 1));
                 if constexpr (Storage<S>::offset) v = raw * (double)p.inv_scale;
                 else v = raw;
             }
@@ -709,6 +704,13 @@ extern "C" int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes) {
     h->mem_bytes = bytes;
     h->buf[0] = h->mem;
     h->buf[1] = h->aa ? h->mem : h->mem + h->popset_bytes;
+#ifdef TLBM_DEBUG_BOUNDS
+    h->kp.dbg_lo = h->mem;
+    h->kp.dbg_hi = h->mem + h->nbuf * h->popset_bytes;
+    h->kp.dbg_count = (unsigned long long*)(h->mem + h->status_off + 64);
+    e = cudaMemset(h->kp.dbg_count, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
+#endif
     set_cur(h, 0);
     // 2D FP16/BF16 storage with two-relaxation-time rates defaults to the
     // shared-memory staged kernel (512-node tiles, 3 stages: the fastest on
@@ -1284,6 +1286,23 @@ extern "C" int tlbm_derived(tlbm_t h, double* out, int cap, int* count) {
     for (int i = 0; i < n && i < cap; ++i) out[i] = v[i];
     if (count) *count = n < cap ? n : cap;
     return TLBM_OK;
+}
+
+extern "C" int tlbm_bounds_violations(tlbm_t h, int64_t* count) {
+    TLBM_CHECK_HANDLE(h);
+    TLBM_CHECK_BOUND(h);
+    if (!count) return fail(h, TLBM_ERR_ARG, "count is NULL");
+#ifdef TLBM_DEBUG_BOUNDS
+    unsigned long long c = 0;
+    cudaError_t e = cudaMemcpyAsync(&c, h->kp.dbg_count, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reading the violation counter");
+    *count = (int64_t)c;
+    return TLBM_OK;
+#else
+    *count = 0;
+    return fail(h, TLBM_ERR_UNSUPPORTED, "this library is built without bounds checks (TLBM_DEBUG_BOUNDS)");
+#endif
 }
 
 extern "C" const char* tlbm_last_error(tlbm_t h) { return h ? h->err : g_create_error; }

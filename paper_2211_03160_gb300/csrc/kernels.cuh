@@ -95,7 +95,35 @@ struct KParams {
         float m3shp, r1, r3, c1, c2, omsp, w0s, was, wbs, f9a, f9b, f3a, f3b;
         float t1, t2, qpwT, hqm, omqp, g0c;
     } tf;
+#ifdef TLBM_DEBUG_BOUNDS
+    // the population buffers of the handle and the violation counter
+    const char* dbg_lo;
+    const char* dbg_hi;
+    unsigned long long* dbg_count;
+#endif
 };
+
+// Bounds check of the debug build (TLBM_DEBUG_BOUNDS; compiled out otherwise):
+// the access of elements q[-before .. n - before) must lie in the population
+// buffers [p.dbg_lo, p.dbg_hi).  One that does not is counted in *p.dbg_count
+// and redirected to element 16 of the buffers (aligned for every vector
+// width), so that nothing outside the allocation is touched.
+// TLBM_DBG(p, q, before, n) is the checked pointer in the debug build and q
+// itself otherwise (a macro, so that the release build's code, including what
+// the compiler knows about pointer aliasing, is exactly the unchecked one).
+#ifdef TLBM_DEBUG_BOUNDS
+template <class T>
+__device__ __forceinline__ T* dbg_ptr(const KParams& p, T* q, int before, int n) {
+    const char* a = reinterpret_cast<const char*>(q - before);
+    if (a >= p.dbg_lo && a + (long long)n * (long long)sizeof(T) <= p.dbg_hi) return q;
+    atomicAdd(p.dbg_count, 1ull);
+    using B = typename std::conditional<std::is_const<T>::value, const char, char>::type;
+    return reinterpret_cast<T*>(const_cast<B*>(p.dbg_lo)) + 16;
+}
+#define TLBM_DBG(p, q, before, n) ::tlbm::dbg_ptr((p), (q), (before), (n))
+#else
+#define TLBM_DBG(p, q, before, n) (q)
+#endif
 
 template <int j, int dy, int dz>
 __device__ __forceinline__ int off_shift(const KParams& p) {
@@ -808,8 +836,8 @@ __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams&
         // where the next AA_EVEN half reads it
         constexpr int plane = MODE == AA_EVEN ? i : o;
         const long long s = MODE == AA_ODD ? L.slot(x, y, z) : L.slot(dx, dy, dz);
-        if constexpr (THERMAL) base[(long long)plane * L.plane + s] = enc_g<S, C>(out, scale);
-        else base[(long long)plane * L.plane + s] = enc_f<LS, S, C>(out, plane, scale);
+        if constexpr (THERMAL) *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_g<S, C>(out, scale);
+        else *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_f<LS, S, C>(out, plane, scale);
     } else {
         // periodic: the value reaches the image node w = wrap(x + e_i) as f_i;
         // written by PULL: slot (w - e_i) of plane i; by AA_EVEN: slot (w - e_i)
@@ -820,8 +848,8 @@ __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams&
         const int wz = oz ? (dz < 0 ? dz + L.nz : dz - L.nz) : dz;
         constexpr int plane = MODE == AA_EVEN ? o : i;
         const long long s = MODE == AA_ODD ? L.slot(wx, wy, wz) : L.slot(wx - ex, wy - ey, wz - ez);
-        if constexpr (THERMAL) base[(long long)plane * L.plane + s] = enc_g<S, C>(val, scale);
-        else base[(long long)plane * L.plane + s] = enc_f<LS, S, C>(val, plane, scale);
+        if constexpr (THERMAL) *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_g<S, C>(val, scale);
+        else *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_f<LS, S, C>(val, plane, scale);
     }
 }
 
@@ -872,14 +900,14 @@ __device__ __forceinline__ void pull_node_vec(const S* __restrict__ own, const K
     static_for<LF::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         C t[VEC];
-        pull_row<S, VEC, LF::e(i, 0), C, CG>(own + p.loff[i], lane, t);
+        pull_row<S, VEC, LF::e(i, 0), C, CG>(TLBM_DBG(p, (own + p.loff[i]), 1, VEC + 2), lane, t);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) f[i][k] = raw_to_dev_k<LF, S, C, KS>(t[k], i, inv_scale);
     });
     static_for<LG::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         C t[VEC];
-        pull_row<S, VEC, LG::e(i, 0), C, CG>(own + p.loff[LF::Q + i], lane, t);
+        pull_row<S, VEC, LG::e(i, 0), C, CG>(TLBM_DBG(p, (own + p.loff[LF::Q + i]), 1, VEC + 2), lane, t);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g_k<S, C, KS>(t[k], inv_scale);
     });
@@ -1003,14 +1031,14 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
             S v[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
-            st_vec<S, VEC>(own + p.soff[i], v);
+            st_vec<S, VEC>(TLBM_DBG(p, (own + p.soff[i]), 0, VEC), v);
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
-            st_vec<S, VEC>(own + p.soff[QF + i], v);
+            st_vec<S, VEC>(TLBM_DBG(p, (own + p.soff[QF + i]), 0, VEC), v);
         });
     } else {
 #pragma unroll
@@ -1018,11 +1046,11 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
             if (x0 + k < L.nx) {
                 static_for<QF>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    own[p.soff[i] + k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                    *TLBM_DBG(p, (own + (p.soff[i] + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
                 });
                 static_for<QG>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    own[p.soff[QF + i] + k] = enc_g_k<S, C, KS>(g[i][k], scale);
+                    *TLBM_DBG(p, (own + (p.soff[QF + i] + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale);
                 });
             }
         }
@@ -1114,17 +1142,18 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
     static_for<QF>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         C t[VEC];
-        if constexpr (MODE == AA_EVEN) pull_row<S, VEC, 0, C>(own_ld + off_shift<i>(p), lane, t);
-        else pull_row<S, VEC, LF::e(i, 0), C>(own_ld + off_shift<LF::opp(i), -LF::e(i, 1), -LF::e(i, 2)>(p), lane, t);
+        if constexpr (MODE == AA_EVEN) pull_row<S, VEC, 0, C>(TLBM_DBG(p, (own_ld + off_shift<i>(p)), 1, VEC + 2), lane, t);
+        else pull_row<S, VEC, LF::e(i, 0), C>(TLBM_DBG(p, (own_ld + off_shift<LF::opp(i), -LF::e(i, 1), -LF::e(i, 2)>(p)), 1, VEC + 2),
+                                               lane, t);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) f[i][k] = raw_to_dev_k<LF, S, C, KS>(t[k], i, inv_scale);
     });
     static_for<QG>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
         C t[VEC];
-        if constexpr (MODE == AA_EVEN) pull_row<S, VEC, 0, C>(own_ld + off_shift<QF + i>(p), lane, t);
-        else pull_row<S, VEC, LG::e(i, 0), C>(own_ld + off_shift<QF + LG::opp(i), -LG::e(i, 1), -LG::e(i, 2)>(p), lane,
-                                               t);
+        if constexpr (MODE == AA_EVEN) pull_row<S, VEC, 0, C>(TLBM_DBG(p, (own_ld + off_shift<QF + i>(p)), 1, VEC + 2), lane, t);
+        else pull_row<S, VEC, LG::e(i, 0), C>(
+                TLBM_DBG(p, (own_ld + off_shift<QF + LG::opp(i), -LG::e(i, 1), -LG::e(i, 2)>(p)), 1, VEC + 2), lane, t);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) g[i][k] = raw_to_g_k<S, C, KS>(t[k], inv_scale);
     });
@@ -1143,14 +1172,14 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
                 S v[VEC];
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
-                st_vec<S, VEC>(own + off_shift<LF::opp(i)>(p), v);
+                st_vec<S, VEC>(TLBM_DBG(p, (own + off_shift<LF::opp(i)>(p)), 0, VEC), v);
             });
             static_for<QG>([&](auto ii) {
                 constexpr int i = decltype(ii)::value;
                 S v[VEC];
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
-                st_vec<S, VEC>(own + off_shift<QF + LG::opp(i)>(p), v);
+                st_vec<S, VEC>(TLBM_DBG(p, (own + off_shift<QF + LG::opp(i)>(p)), 0, VEC), v);
             });
         } else {
 #pragma unroll
@@ -1158,27 +1187,34 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
                 if (x0 + k < L.nx) {
                     static_for<QF>([&](auto ii) {
                         constexpr int i = decltype(ii)::value;
-                        own[off_shift<LF::opp(i)>(p) + k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                        *TLBM_DBG(p, (own + (off_shift<LF::opp(i)>(p) + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
                     });
                     static_for<QG>([&](auto ii) {
                         constexpr int i = decltype(ii)::value;
-                        own[off_shift<QF + LG::opp(i)>(p) + k] = enc_g_k<S, C, KS>(g[i][k], scale);
+                        *TLBM_DBG(p, (own + (off_shift<QF + LG::opp(i)>(p) + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale);
                     });
                 }
             }
         }
     } else {
-        // push to x + e_i of plane i (all lanes take part in the shuffles)
+        // push to x + e_i of plane i (all lanes take part in the shuffles; lanes
+        // past the row end store nothing)
+#ifdef TLBM_DEBUG_BOUNDS
+#define TLBM_AIM(q) (x0 < L.nx ? TLBM_DBG(p, (q), 1, VEC + 2) : (q))
+#else
+#define TLBM_AIM(q) (q)
+#endif
         static_for<QF>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            push_row<S, VEC, LF::e(i, 0), C>(own + off_shift<i, LF::e(i, 1), LF::e(i, 2)>(p), lane, x0, L.nx, f[i],
+            push_row<S, VEC, LF::e(i, 0), C>(TLBM_AIM((own + off_shift<i, LF::e(i, 1), LF::e(i, 2)>(p))), lane, x0, L.nx, f[i],
                                              [&](C d) { return enc_f_k<LF, S, C, KS>(d, i, scale); });
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            push_row<S, VEC, LG::e(i, 0), C>(own + off_shift<QF + i, LG::e(i, 1), LG::e(i, 2)>(p), lane, x0, L.nx, g[i],
+            push_row<S, VEC, LG::e(i, 0), C>(TLBM_AIM((own + off_shift<QF + i, LG::e(i, 1), LG::e(i, 2)>(p))), lane, x0, L.nx, g[i],
                                              [&](C d) { return enc_g_k<S, C, KS>(d, scale); });
         });
+#undef TLBM_AIM
         if (x0 >= L.nx) return;
     }
     wall_writes<DIM, S, VEC, C, KS, MODE>(buf, p, x0, y, z, f, g);
@@ -1213,7 +1249,7 @@ __device__ __forceinline__ void fetch_row(const S* __restrict__ own, const KPara
     static_for<LF::Q + LG::Q>([&](auto jj) {
         constexpr int j = decltype(jj)::value;
         constexpr int ex = j < LF::Q ? LF::e(j < LF::Q ? j : 0, 0) : LG::e(j < LF::Q ? 0 : j - LF::Q, 0);
-        const S* __restrict__ q = own + p.loff[j];
+        const S* __restrict__ q = TLBM_DBG(p, (own + p.loff[j]), 1, VEC + 2);
         if constexpr (VEC == 1) {
             r.v[j][0] = q[-ex];
         } else {
@@ -1282,14 +1318,14 @@ __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p
             S v[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
-            st_vec<S, VEC>(own + p.soff[i], v);
+            st_vec<S, VEC>(TLBM_DBG(p, (own + p.soff[i]), 0, VEC), v);
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
-            st_vec<S, VEC>(own + p.soff[QF + i], v);
+            st_vec<S, VEC>(TLBM_DBG(p, (own + p.soff[QF + i]), 0, VEC), v);
         });
     } else {
 #pragma unroll
@@ -1297,11 +1333,11 @@ __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p
             if (x0 + k < L.nx) {
                 static_for<QF>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    own[p.soff[i] + k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                    *TLBM_DBG(p, (own + (p.soff[i] + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
                 });
                 static_for<QG>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    own[p.soff[QF + i] + k] = enc_g_k<S, C, KS>(g[i][k], scale);
+                    *TLBM_DBG(p, (own + (p.soff[QF + i] + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale);
                 });
             }
         }
@@ -1387,12 +1423,12 @@ __device__ __forceinline__ void pull_node(const S* __restrict__ src, const KPara
     const S* __restrict__ gsrc = src + (long long)LF::Q * L.plane;
     static_for<LF::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        const C raw = to_c<C>(src[pre_index<LF, i>(p, x, y, z)]);
+        const C raw = to_c<C>(*TLBM_DBG(p, (src + pre_index<LF, i>(p, x, y, z)), 0, 1));
         f[i] = raw_to_dev<LF, S, C>(raw, i, inv_scale);
     });
     static_for<LG::Q>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        const C raw = to_c<C>(gsrc[pre_index<LG, i>(p, x, y, z)]);
+        const C raw = to_c<C>(*TLBM_DBG(p, (gsrc + pre_index<LG, i>(p, x, y, z)), 0, 1));
         g[i] = raw_to_g<S, C>(raw, inv_scale);
     });
 }

@@ -190,7 +190,15 @@ extern "C" int tlbm_reduce_noalloc(tlbm_t h, const void* state, double* out) {
     double* scratch = nullptr;
     cudaError_t e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) return na_fail(h, TLBM_ERR_CUDA, "cudaGetSymbolAddress", cudaGetErrorString(e));
-    e = launch_partials_any(h->dim, h->prec, buf, h->kp, scratch, (int)slots, h->stream);
+    KParams kp = h->kp;
+#ifdef TLBM_DEBUG_BOUNDS
+    // the checks cover the state actually read; with no bound block its
+    // violations land in the static scratch and go unreported
+    kp.dbg_lo = (const char*)buf;
+    kp.dbg_hi = (const char*)buf + h->popset_bytes;
+    if (!h->mem) kp.dbg_count = reinterpret_cast<unsigned long long*>(scratch + (long long)NA_SLOTS * NA_FIELDS + 7);
+#endif
+    e = launch_partials_any(h->dim, h->prec, buf, kp, scratch, (int)slots, h->stream);
     if (e != cudaSuccess) return na_fail(h, TLBM_ERR_CUDA, "partial-sum kernel", cudaGetErrorString(e));
     noalloc_final<<<1, NA_FINAL_THREADS, 0, h->stream>>>(scratch, (int)slots);
     e = cudaGetLastError();

@@ -191,7 +191,8 @@ __global__ void __maxnreg__(NC == 8 ? 112 : 168)
             }
             __syncwarp();
             if (lane < Q)
-                bulk_copy_g2s(stages + s * STAGE + lane * LW, src + L.row(y, (int)z) + p.loff[lane] + lo, bytes,
+                bulk_copy_g2s(stages + s * STAGE + lane * LW,
+                              TLBM_DBG(p, (src + L.row(y, (int)z) + p.loff[lane] + lo), 0, (int)(bytes / sizeof(S))), bytes,
                               &full[s]);
             if (++s == NS) {
                 s = 0;
@@ -257,22 +258,22 @@ __global__ void __maxnreg__(NC == 8 ? 112 : 168)
         if (xr + 1 < tw) {
             static_for<QF>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
-                *reinterpret_cast<S2*>(own + p.soff[q]) =
+                *reinterpret_cast<S2*>(TLBM_DBG(p, (own + p.soff[q]), 0, 2)) =
                     P2::pack(enc_val_f<LF, S, KS>(fd[q].x, q, scale), enc_val_f<LF, S, KS>(fd[q].y, q, scale));
             });
             static_for<QG>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
-                *reinterpret_cast<S2*>(own + p.soff[QF + q]) =
+                *reinterpret_cast<S2*>(TLBM_DBG(p, (own + p.soff[QF + q]), 0, 2)) =
                     P2::pack(enc_val_g<S, KS>(gd[q].x, scale), enc_val_g<S, KS>(gd[q].y, scale));
             });
         } else {
             static_for<QF>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
-                own[p.soff[q]] = enc_f_k<LF, S, float, KS>(fd[q].x, q, scale);
+                *TLBM_DBG(p, (own + p.soff[q]), 0, 1) = enc_f_k<LF, S, float, KS>(fd[q].x, q, scale);
             });
             static_for<QG>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
-                own[p.soff[QF + q]] = enc_g_k<S, float, KS>(gd[q].x, scale);
+                *TLBM_DBG(p, (own + p.soff[QF + q]), 0, 1) = enc_g_k<S, float, KS>(gd[q].x, scale);
             });
         }
         float f2[QF][2], g2[QG][2];

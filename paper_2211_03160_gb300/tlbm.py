@@ -82,6 +82,7 @@ _SIGS = {
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "tlbm_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "tlbm_bounds_violations": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "tlbm_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "tlbm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_double]),
     "tlbm_batch_set_wait_limit": (C.c_int, [C.c_void_p, C.c_double]),
@@ -128,21 +129,28 @@ _SIGS = {
 }
 
 
+def _debug_bounds() -> bool:
+    return os.environ.get("TLBM_DEBUG_BOUNDS") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    """libtlbm.so, or libtlbm_debug.so (every kernel access bounds-checked)
+    when the environment sets TLBM_DEBUG_BOUNDS=1."""
+    return _build.LIB_DEBUG if _debug_bounds() else _build.LIB
 
 
 def lib(build_if_missing: bool = True):
-    """Load libtlbm.so (building it first if it is missing or stale).  Raises
-    if the library cannot be built or loaded: there is no fallback path."""
+    """Load the library (building it first if it is missing or stale).  Raises
+    if it cannot be built or loaded: there is no fallback path."""
     global _lib
     with _lock:
         if _lib is None:
+            path = library_path()
             if build_if_missing:
-                _build.build()
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError(f"libtlbm.so not found at {_build.LIB}; run the build first")
-            L = C.CDLL(_build.LIB)
+                _build.build(debug=_debug_bounds())
+            if not os.path.exists(path):
+                raise RuntimeError(f"{os.path.basename(path)} not found at {path}; run the build first")
+            L = C.CDLL(path)
             for name, (res, args) in _SIGS.items():
                 fn = getattr(L, name, None)
                 if fn is None:
@@ -330,6 +338,12 @@ def tlbm_set_staged(h, tile_width=0, stages=0):
 
 def tlbm_set_wait_limit(h, seconds):
     _check(h, lib().tlbm_set_wait_limit(h, float(seconds)))
+
+
+def tlbm_bounds_violations(h) -> int:
+    n = C.c_int64()
+    _check(h, lib().tlbm_bounds_violations(h, C.byref(n)))
+    return n.value
 
 
 def tlbm_save(h, path):
