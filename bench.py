@@ -394,6 +394,51 @@ def cpu_baseline(target_seconds: float = 12.0) -> dict:
                       f"{oracle.get_threads()} OpenMP threads"}
 
 
+def _host_available_bytes() -> int:
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def cpu_extended() -> dict:
+    """The oracle's own speed at the measurement cases: one thread on the
+    129^2 FP64 case (2000 steps), and all host cores on 10 steps of the 8193^2
+    and 385^3 workloads (FP64, two population buffers).  A full-size case runs
+    only when the host has three times its memory available."""
+    from oracle import oracle
+
+    cores = os.cpu_count() or 1
+    out = {"cores": cores}
+    oracle.set_threads(1)
+    s = oracle.Sim(129, 129, Ra=1e5, Pr=0.71, Ma=0.1)
+    s.init(1, 1e-3)
+    t0 = time.perf_counter()
+    s.step(2000)
+    el = time.perf_counter() - t0
+    s.close()
+    out["129sq_fp64_1_thread_mlups"] = 129 * 129 * 2000 / el / 1e6
+    oracle.set_threads(cores)
+    for name, (nx, ny, nz, lattice, Ra, q) in {"8193sq": (8193, 8193, 1, oracle.D2Q9_D2Q5, 1e8, 14),
+                                             "385cube": (385, 385, 385, oracle.D3Q19_D3Q7, 1e7, 26)}.items():
+        need = 2 * q * 8 * nx * ny * nz
+        if _host_available_bytes() < 3 * need:
+            out[f"{name}_fp64_all_cores_mlups"] = None
+            continue
+        s = oracle.Sim(nx, ny, nz, lattice=lattice, Ra=Ra, Pr=0.71, Ma=0.1)
+        s.init(2 if nz == 1 else 3, 1e-3)
+        t0 = time.perf_counter()
+        s.step(10)
+        el = time.perf_counter() - t0
+        s.close()
+        out[f"{name}_fp64_all_cores_mlups"] = nx * ny * nz * 10 / el / 1e6
+    return out
+
+
 def run_reference(args):
     """The oracle timed as the reference arm: each step is one oracle time step
     on a 513 x 513 sample of the headline workload's physics."""
@@ -440,6 +485,8 @@ def main():
                                           "batch64_fp32,batch64_fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time the oracle single-threaded at 129^2 and on all cores at full size")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -493,6 +540,8 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+        if args.cpu_full:
+            cpu["extended"] = cpu_extended()
 
     if rank != 0:
         return 0
