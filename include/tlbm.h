@@ -177,10 +177,12 @@ TLBM_API int tlbm_macros(tlbm_t h, void* rho, void* ux, void* uy, void* uz, void
 /* Nusselt number of the current state, FP64 deterministic reduction:
  * Nu = 1 + L <u_h T> / (alpha dT), u_h the velocity component along the
  * heat-flux axis (vertical for RB, x for side-heated) and L the cell extent
- * along it.  Synchronises the stream. */
+ * along it.  Synchronises the stream.  TLBM_ERR_DIVERGED (the value still
+ * written) if the same reduction finds a non-finite value or |u| > 0.5. */
 TLBM_API int tlbm_nusselt(tlbm_t h, double* nu);
 
-/* Kinetic energy sum 1/2 rho |u|^2 and mass sum rho, FP64.  Synchronises. */
+/* Kinetic energy sum 1/2 rho |u|^2 and mass sum rho, FP64.  Synchronises.
+ * TLBM_ERR_DIVERGED (the values still written) as for tlbm_nusselt. */
 TLBM_API int tlbm_energy(tlbm_t h, double* ekin, double* mass);
 
 /* Copy the canonical pre-collision populations (FP64, dense layout above) to
@@ -219,7 +221,8 @@ TLBM_API int tlbm_save(tlbm_t h, const char* path);
 TLBM_API int tlbm_load(tlbm_t h, const char* path);
 
 /* *diverged = 1 if the state holds a non-finite value or |u| > 0.5; *step =
- * current time step.  Runs a reduction; synchronises.  Either output may be NULL. */
+ * current time step.  Runs a reduction; synchronises.  Either output may be
+ * NULL.  Reports divergence through *diverged, returning TLBM_OK. */
 TLBM_API int tlbm_status(tlbm_t h, int* diverged, int64_t* step);
 
 /* Derived parameters: out[0..6] = U, H, nu, alpha, gbeta, a_T, omega, then the
@@ -319,7 +322,9 @@ TLBM_API int tlbm_batch_autotune(tlbm_batch_t b, int trials);
  * collision form and size class floor(log2(total nodes)), if any.) */
 /* Borrow instance idx as a single-cell handle (owned by the batch). */
 TLBM_API int tlbm_batch_instance(tlbm_batch_t b, int idx, tlbm_t* out);
-/* Per-instance Nusselt numbers / divergence flags into nu[n] / diverged[n]. */
+/* Per-instance Nusselt numbers / divergence flags into nu[n] / diverged[n].
+ * tlbm_batch_nusselt writes every value and returns TLBM_ERR_DIVERGED if any
+ * instance has diverged (tlbm_batch_status says which). */
 TLBM_API int tlbm_batch_nusselt(tlbm_batch_t b, double* nu);
 TLBM_API int tlbm_batch_status(tlbm_batch_t b, int* diverged);
 /* tlbm_macros of instance idx. */

@@ -897,6 +897,9 @@ static int run_reduce(tlbm_t h, double* res) {
     return TLBM_OK;
 }
 
+// the reduction found a non-finite value or |u| > 0.5 (|u|^2 > 0.25)
+static bool reduce_diverged(const double* r) { return r[4] != 0.0 || !(r[3] <= 0.25); }
+
 extern "C" int tlbm_nusselt(tlbm_t h, double* nu) {
     TLBM_CHECK_HANDLE(h);
     TLBM_CHECK_BOUND(h);
@@ -908,6 +911,7 @@ extern "C" int tlbm_nusselt(tlbm_t h, double* nu) {
     const int ax = h->kp.heat_axis;
     const double L = ax == 0 ? h->nx : (ax == 1 ? h->ny : h->nz);
     *nu = 1.0 + L * (r[0] / N) / (h->alpha * (h->prm.Th - h->prm.Tc));
+    if (reduce_diverged(r)) return fail(h, TLBM_ERR_DIVERGED, "the state has diverged (the value is written)");
     return TLBM_OK;
 }
 
@@ -919,6 +923,7 @@ extern "C" int tlbm_energy(tlbm_t h, double* ekin, double* mass) {
     if (rc) return rc;
     if (ekin) *ekin = r[1];
     if (mass) *mass = r[2];
+    if (reduce_diverged(r)) return fail(h, TLBM_ERR_DIVERGED, "the state has diverged (the values are written)");
     return TLBM_OK;
 }
 
@@ -928,7 +933,7 @@ extern "C" int tlbm_status(tlbm_t h, int* diverged, int64_t* step) {
     double r[RED_FIELDS];
     int rc = run_reduce(h, r);
     if (rc) return rc;
-    if (diverged) *diverged = (r[4] != 0.0 || !(r[3] <= 0.25)) ? 1 : 0;
+    if (diverged) *diverged = reduce_diverged(r) ? 1 : 0;
     if (step) *step = h->t;
     return TLBM_OK;
 }

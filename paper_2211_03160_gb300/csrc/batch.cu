@@ -637,10 +637,18 @@ extern "C" int tlbm_batch_instance(tlbm_batch_t b, int idx, tlbm_t* out) {
 extern "C" int tlbm_batch_nusselt(tlbm_batch_t b, double* nu) {
     if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
     if (!nu) return bfail(b, TLBM_ERR_ARG, "nu is NULL");
+    int first_diverged = -1;
     for (int i = 0; i < b->n; ++i) {
         int rc = tlbm_nusselt(b->inst[i], &nu[i]);
-        if (rc != TLBM_OK) return bfail(b, rc, "instance %d: %s", i, tlbm_last_error(b->inst[i]));
+        if (rc == TLBM_ERR_DIVERGED) {
+            if (first_diverged < 0) first_diverged = i;
+        } else if (rc != TLBM_OK) {
+            return bfail(b, rc, "instance %d: %s", i, tlbm_last_error(b->inst[i]));
+        }
     }
+    if (first_diverged >= 0)
+        return bfail(b, TLBM_ERR_DIVERGED, "instance %d (and maybe others) has diverged; every value is written",
+                      first_diverged);
     return TLBM_OK;
 }
 

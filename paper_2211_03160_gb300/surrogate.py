@@ -315,7 +315,7 @@ def evaluate(net: ConvNet, draw_list, run_tf: float, ref_tf: float, samples_per_
     nus = np.zeros((2 * n, total))
     for s_ in range(total):
         b.step(dt)
-        nus[:, s_] = b.nusselt()
+        nus[:, s_] = b.nusselt(allow_diverged=True)  # the status is recorded below
     status = b.status()
     b.close()
     window = samples_per_tf // 2  # half a free-fall time

@@ -220,15 +220,20 @@ def tlbm_macros(h, rho=None, ux=None, uy=None, uz=None, T=None, out_dtype=TLBM_O
     _check(h, lib().tlbm_macros(h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T), int(out_dtype)))
 
 
-def tlbm_nusselt(h) -> float:
+def tlbm_nusselt(h, allow_diverged: bool = False) -> float:
+    """allow_diverged: return the value of a diverged state instead of raising."""
     v = C.c_double()
-    _check(h, lib().tlbm_nusselt(h, C.byref(v)))
+    rc = lib().tlbm_nusselt(h, C.byref(v))
+    if not (allow_diverged and rc == TLBM_ERR_DIVERGED):
+        _check(h, rc)
     return v.value
 
 
-def tlbm_energy(h):
+def tlbm_energy(h, allow_diverged: bool = False):
     e, m = C.c_double(), C.c_double()
-    _check(h, lib().tlbm_energy(h, C.byref(e), C.byref(m)))
+    rc = lib().tlbm_energy(h, C.byref(e), C.byref(m))
+    if not (allow_diverged and rc == TLBM_ERR_DIVERGED):
+        _check(h, rc)
     return e.value, m.value
 
 
@@ -443,11 +448,11 @@ class Sim:
             out["uz"].zero_()
         return out
 
-    def nusselt(self):
-        return tlbm_nusselt(self.h)
+    def nusselt(self, allow_diverged=False):
+        return tlbm_nusselt(self.h, allow_diverged)
 
-    def energy(self):
-        return tlbm_energy(self.h)
+    def energy(self, allow_diverged=False):
+        return tlbm_energy(self.h, allow_diverged)
 
     def status(self):
         return tlbm_status(self.h)
@@ -583,9 +588,11 @@ def tlbm_batch_instance(b, idx: int):
     return h
 
 
-def tlbm_batch_nusselt(b, n: int) -> list:
+def tlbm_batch_nusselt(b, n: int, allow_diverged: bool = False) -> list:
     out = (C.c_double * n)()
-    _bcheck(b, lib().tlbm_batch_nusselt(b, out))
+    rc = lib().tlbm_batch_nusselt(b, out)
+    if not (allow_diverged and rc == TLBM_ERR_DIVERGED):
+        _bcheck(b, rc)
     return list(out)
 
 
@@ -668,8 +675,8 @@ class Batch:
     def set_wait_limit(self, seconds):
         tlbm_batch_set_wait_limit(self.b, seconds)
 
-    def nusselt(self):
-        return tlbm_batch_nusselt(self.b, self.n)
+    def nusselt(self, allow_diverged=False):
+        return tlbm_batch_nusselt(self.b, self.n, allow_diverged)
 
     def status(self):
         return tlbm_batch_status(self.b, self.n)

@@ -273,8 +273,45 @@ def test_divergence_is_reported(T):
     g.set_populations(f, gg)
     div, _ = g.status()
     assert div
+    with pytest.raises(T.TlbmError) as ei:
+        g.nusselt()
+    assert ei.value.code == T.TLBM_ERR_DIVERGED
+    assert g.nusselt(allow_diverged=True) == 1.0  # T = 0 everywhere
     g.init(1, 1e-3)
     assert not g.status()[0]
+    g.nusselt()
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, FP16, BF16])
+def test_non_finite_state_is_reported(T, prec):
+    """A NaN in the host buffer of tlbm_set_populations is found by the next
+    reduction: tlbm_status flags it, tlbm_energy returns TLBM_ERR_DIVERGED, and
+    a batch reports the one diverged instance."""
+    g = T.Sim(24, 20, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec)
+    g.init(2, 1e-3)
+    f, gg = g.get_populations()
+    f[4, 7, 9] = np.nan
+    g.set_populations(f, gg)
+    g.step(2)
+    assert g.status()[0]
+    with pytest.raises(T.TlbmError) as ei:
+        g.energy()
+    assert ei.value.code == T.TLBM_ERR_DIVERGED
+    g.close()
+    inst = [(17, 17, 1, 1e5, 0.71, 0.1, 1), (19, 17, 1, 1e5, 0.71, 0.1, 2)]
+    b = T.Batch(inst, lattice=D2, precision=prec)
+    b.init(1e-3)
+    f, gg = b.get_populations(1)
+    f[0, 3, 3] = np.inf
+    T.tlbm_set_populations(b.instance(1), f, gg)
+    b.step(1)
+    assert b.status() == [False, True]
+    with pytest.raises(T.TlbmError) as ei:
+        b.nusselt()
+    assert ei.value.code == T.TLBM_ERR_DIVERGED
+    nu = b.nusselt(allow_diverged=True)
+    assert np.isfinite(nu[0]) and not np.isfinite(nu[1])
+    b.close()
 
 
 def test_staged_at_bench_size(T):
