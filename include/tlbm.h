@@ -62,9 +62,10 @@ enum tlbm_status_code {
 
 enum tlbm_lattice { TLBM_D2Q9_D2Q5 = 0, TLBM_D3Q19_D3Q7 = 1 };
 
-/* Storage precision of the populations.  FP16/BF16 "offset" storage keeps
- * f_i - w_i (flow) and g_i (temperature, T0 = 0) scaled by a power of two;
- * collision then runs in FP32.  FP64 storage collides in FP64. */
+/* Storage precision of the populations.  FP32, FP16 and BF16 storage keep
+ * the flow deviations f_i - w_i and g_i (temperature, T0 = 0), FP16/BF16
+ * ("offset" storage) scaled by a power of two; collision then runs in FP32.
+ * FP64 storage keeps f_i and g_i and collides in FP64. */
 enum tlbm_prec { TLBM_FP64 = 0, TLBM_FP32 = 1, TLBM_FP16_OFFSET = 2, TLBM_BF16_OFFSET = 3 };
 
 /* Wall configuration.  RB: hot bottom (Th), cold top (Tc), adiabatic sides.
@@ -205,7 +206,7 @@ TLBM_API int tlbm_set_populations(tlbm_t h, const double* host_f, const double* 
  * body force, the derived parameters of tlbm_derived, the step counter, the
  * node count) followed by the pre-collision populations in FP64 in the layout
  * of tlbm_get_populations (flow planes, then thermal planes, each nx*ny*nz
- * values, x fastest), native byte order; with FP16/BF16-offset storage the
+ * values, x fastest), native byte order; with FP32, FP16 or BF16 storage the
  * flow planes hold the deviations f_i - w_i (a header flag says so), the exact
  * FP64 image of what the storage holds.  Written in chunks through the scratch
  * of the bound block (no full host copy).  TLBM_ERR_ARG if path is NULL or

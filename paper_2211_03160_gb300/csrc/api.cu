@@ -1075,7 +1075,7 @@ static void ckpt_fill(tlbm_t h, CkptHeader& c) {
     int n = 0;
     tlbm_derived(h, c.derived, 7 + MAXQ + 7, &n);
     c.nderived = n;
-    c.flow_dev = (h->prec == TLBM_FP16_OFFSET || h->prec == TLBM_BF16_OFFSET) ? 1 : 0;
+    c.flow_dev = h->prec == TLBM_FP64 ? 0 : 1;  // offset storage (FP32, FP16, BF16)
     c.t = h->t;
     c.nodes = (int64_t)h->nx * h->ny * h->nz;
 }

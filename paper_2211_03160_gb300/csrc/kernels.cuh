@@ -142,26 +142,40 @@ __device__ __forceinline__ int off_shift(const struct KParams& p);
 
 template <class S>
 struct Storage;
+// offset: the flow planes hold the deviations d_i = f_i - w_i (times the
+// storage scale) rather than f_i, so that a stored value keeps the precision of
+// the deviation instead of rounding at the ulp of w_i; scaled: that scale may
+// differ from 1 (FP32 deviations are stored as they are).
 template <>
 struct Storage<double> {
     using C = double;
     static constexpr bool offset = false;
+    static constexpr bool scaled = false;
 };
 template <>
 struct Storage<float> {
     using C = float;
-    static constexpr bool offset = false;
+    static constexpr bool offset = true;
+    static constexpr bool scaled = false;
 };
 template <>
 struct Storage<__half> {
     using C = float;
     static constexpr bool offset = true;
+    static constexpr bool scaled = true;
 };
 template <>
 struct Storage<__nv_bfloat16> {
     using C = float;
     static constexpr bool offset = true;
+    static constexpr bool scaled = true;
 };
+
+// The collision works on the stored values directly (KS) with two-relaxation-
+// time rates on offset storage; it has to unscale them only if the storage
+// scale may differ from 1.
+template <class S, bool TRT>
+constexpr bool collide_scaled = TRT && Storage<S>::offset && Storage<S>::scaled;
 
 template <class C, class S>
 __device__ __forceinline__ C to_c(S s) {
@@ -1021,7 +1035,7 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
     C f[QF][VEC], g[QG][VEC];
     pull_node_vec<DIM, S, VEC, C, KS, CG>(src + row + x0ld, p, lane, f, g);
 
-    collide_vec<DIM, TRT, C, KS, VEC>(f, g, p);
+    collide_vec<DIM, TRT, C, collide_scaled<S, TRT>, VEC>(f, g, p);
 
     if (x0 >= L.nx) return;
     S* __restrict__ own = dst + row + x0;
@@ -1160,7 +1174,7 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
 
     // 2D: constants formed on the host (1.6 % faster for 2D FP32 on GB300, 1 %
     // slower for 3D FP16)
-    collide_vec<DIM, TRT, C, KS, VEC, DIM == 2>(f, g, p);
+    collide_vec<DIM, TRT, C, collide_scaled<S, TRT>, VEC, DIM == 2>(f, g, p);
 
     S* own = buf + row + x0;
     if constexpr (MODE == AA_EVEN) {
@@ -1309,7 +1323,7 @@ __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p
     constexpr int QF = LF::Q, QG = LG::Q;
     const Layout& L = p.L;
     const C scale = ScaleOf<C>::s(p);
-    collide_vec<DIM, TRT, C, KS, VEC>(f, g, p);
+    collide_vec<DIM, TRT, C, collide_scaled<S, TRT>, VEC>(f, g, p);
     if (x0 >= L.nx) return;
     S* __restrict__ own = dst + row + x0;
     if (x0 + VEC <= L.nx) {

@@ -253,7 +253,7 @@ __global__ void __maxnreg__(NC == 8 ? 112 : 168)
             ph ^= 1;
         }
         if (!active) continue;
-        collide_trt_v<DIM, float2, KS, true>(fd, gd, p);
+        collide_trt_v<DIM, float2, collide_scaled<S, true>, true>(fd, gd, p);
         S* own = dst + L.row(y, z) + x0 + xr;
         if (xr + 1 < tw) {
             static_for<QF>([&](auto ii) {
