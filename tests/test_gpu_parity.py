@@ -245,6 +245,38 @@ def test_full_size_sampled_windows(T, O, prec, tol):
     assert not div and step == 6
 
 
+@pytest.mark.parametrize("prec,tol", [(FP32, 3e-6), (FP16, 3e-3)])
+def test_full_size_sampled_windows_3d(T, O, prec, tol):
+    """385^3 at Ra = 1e7 in the benchmark's launch configuration: after a few
+    steps, 12^3 windows at corners, on every face and in the interior are read
+    back; one oracle step on each window (with the full cell's parameters) must
+    match the GPU's next state on the window's inner nodes."""
+    n, w = 385, 12
+    g = T.Sim(n, n, n, lattice=D3, Ra=1e7, Pr=0.71, Ma=0.1, precision=prec)
+    d = g.derived()
+    g.init(3, 1e-3)
+    g.step(5)
+    e = n - w
+    boxes = [(0, 0, 0), (e, e, e), (186, 0, 186), (0, 186, 186), (186, 186, 0), (186, 186, e), (e, 100, 250),
+             (186, e, 40), (186, 186, 186), (0, e, 0)]
+    before = [g.get_window(x0, y0, z0, w, w, w) for x0, y0, z0 in boxes]
+    g.step(1)
+    after = [g.get_window(x0, y0, z0, w, w, w) for x0, y0, z0 in boxes]
+    for (x0, y0, z0), (f0, g0), (f1, g1) in zip(boxes, before, after):
+        o = O.Sim(w, w, w, lattice=D3, Ra=1e7, Pr=0.71, Ma=0.1, nu=d["nu"], alpha=d["alpha"], gbeta=d["gbeta"])
+        o.set_populations(f0, g0)
+        o.step(1)
+        fo, go = o.get_populations()
+        # inner nodes: drop a side only where it is an artificial window edge
+        sl = [slice(0 if c0 == 0 else 1, w if c0 + w == n else w - 1) for c0 in (x0, y0, z0)]
+        ef = np.abs(f1[:, sl[2], sl[1], sl[0]] - fo[:, sl[2], sl[1], sl[0]]).max() / np.abs(fo).max()
+        eg = np.abs(g1[:, sl[2], sl[1], sl[0]] - go[:, sl[2], sl[1], sl[0]]).max() / np.abs(go).max()
+        assert ef < tol and eg < tol, ((x0, y0, z0), ef, eg)
+    div, step = g.status()
+    assert not div and step == 6
+    g.close()
+
+
 def test_mass_conserved_on_gpu(T):
     """FP64 storage: sum rho is constant to round-off over 1000 steps."""
     g = T.Sim(257, 129, lattice=D2, Ra=1e6, Pr=0.71, Ma=0.1, precision=FP64)
