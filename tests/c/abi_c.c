@@ -1,6 +1,7 @@
 /* The C ABI used from plain C (no Python, no torch): argument checks and the
  * memory contract without a GPU ("host"), then a short run with caller-owned
- * device memory ("gpu").  Exit status 0 on success; each failed check prints a
+ * device memory and a checkpoint round trip ("gpu", with the checkpoint path).
+ * Exit status 0 on success; each failed check prints a
  * line and makes it 1. */
 #include <math.h>
 #include <stdio.h>
@@ -84,7 +85,43 @@ static double run(int streaming, int steps, double* mass0, double* mass1) {
     return nu;
 }
 
-static int gpu_checks(void) {
+/* checkpoint round trip: save after 40 steps, step on; a second handle loads
+ * the file and steps on as well; the states must agree bit for bit */
+static void checkpoint_check(const char* path) {
+    tlbm_t h[2] = {NULL, NULL};
+    void* mem[2] = {NULL, NULL};
+    size_t bytes = 0;
+    for (int k = 0; k < 2; ++k) {
+        CHECK(tlbm_create(&h[k], 48, 24, 1, TLBM_D2Q9_D2Q5, 1e5, 0.71, 0.1, TLBM_FP16_OFFSET, NULL) == TLBM_OK,
+              "create");
+        tlbm_required_bytes(h[k], &bytes);
+        CHECK(cudaMalloc(&mem[k], bytes) == cudaSuccess, "cudaMalloc");
+        CHECK(tlbm_bind_memory(h[k], mem[k], bytes) == TLBM_OK, "bind");
+    }
+    CHECK(tlbm_init(h[0], 9, 1e-3) == TLBM_OK, "init");
+    CHECK(tlbm_step(h[0], 40) == TLBM_OK, "step");
+    CHECK(tlbm_save(h[0], path) == TLBM_OK, "save: %s", tlbm_last_error(h[0]));
+    CHECK(tlbm_step(h[0], 17) == TLBM_OK, "step");
+    CHECK(tlbm_load(h[1], path) == TLBM_OK, "load: %s", tlbm_last_error(h[1]));
+    int64_t t = 0;
+    CHECK(tlbm_status(h[1], NULL, &t) == TLBM_OK && t == 40, "step counter after load");
+    CHECK(tlbm_step(h[1], 17) == TLBM_OK, "step");
+    const size_t n = (size_t)48 * 24;
+    double* f[2];
+    for (int k = 0; k < 2; ++k) {
+        f[k] = (double*)malloc(9 * n * sizeof(double));
+        CHECK(tlbm_get_populations(h[k], f[k], NULL) == TLBM_OK, "get populations");
+    }
+    CHECK(memcmp(f[0], f[1], 9 * n * sizeof(double)) == 0, "resumed state differs");
+    for (int k = 0; k < 2; ++k) {
+        free(f[k]);
+        tlbm_destroy(h[k]);
+        cudaFree(mem[k]);
+    }
+    remove(path);
+}
+
+static int gpu_checks(const char* path) {
     double m0 = 0, m1 = 0, m2 = 0, m3 = 0;
     const double a = run(TLBM_STREAM_PULL, 301, &m0, &m1);
     const double b = run(TLBM_STREAM_INPLACE, 301, &m2, &m3);
@@ -92,6 +129,7 @@ static int gpu_checks(void) {
     CHECK(a == b, "two-buffer and in-place Nusselt numbers differ: %.17g vs %.17g", a, b);
     CHECK(a > 0.99 && a < 5.0, "Nusselt number %g", a);
     printf("nusselt %.17g %.17g mass %.17g\n", a, b, m1);
+    checkpoint_check(path);
     return failures;
 }
 
@@ -99,7 +137,7 @@ int main(int argc, char** argv) {
     if (argc < 2) return 2;
     int rc = 0;
     if (!strcmp(argv[1], "host")) rc = host_checks();
-    else if (!strcmp(argv[1], "gpu")) rc = host_checks() + gpu_checks();
+    else if (!strcmp(argv[1], "gpu") && argc > 2) rc = host_checks() + gpu_checks(argv[2]);
     else return 2;
     printf("%s: %d failure(s)\n", argv[1], rc);
     return rc ? 1 : 0;

@@ -35,10 +35,10 @@ def test_c_program_host_checks(exe):
 
 
 @pytest.mark.gpu
-def test_c_program_gpu_run(exe):
+def test_c_program_gpu_run(exe, tmp_path):
     import torch
 
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    r = subprocess.run([exe, "gpu"], capture_output=True, text=True, timeout=300)
+    r = subprocess.run([exe, "gpu", str(tmp_path / "c.ckpt")], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
