@@ -40,10 +40,12 @@ def _maxerr(a, b, keys=("rho", "ux", "uy", "uz", "T")):
 
 # ------------------------------------------------------------------ FP64 headline parity
 
-def test_fp64_2d_config1_1000_2000_steps(T, O):
-    """129^2, Ra = 1e5, Pr = 0.71, Ma = 0.1, RB walls, noise 1e-3, seed 1."""
-    g = T.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64)
-    o = O.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1)
+@pytest.mark.parametrize("kw", [{}, {"streaming": 1}, {"walls": 1}], ids=["pull", "inplace", "side_heated"])
+def test_fp64_2d_config1_1000_2000_steps(T, O, kw):
+    """129^2, Ra = 1e5, Pr = 0.71, Ma = 0.1, RB walls, noise 1e-3, seed 1; the
+    same with in-place streaming, and in the side-heated cavity."""
+    g = T.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64, **kw)
+    o = O.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, **{k: v for k, v in kw.items() if k != "streaming"})
     g.init(1, 1e-3)
     o.init(1, 1e-3)
     e0 = _maxerr(_fields(g), o.macros())
@@ -62,10 +64,11 @@ def test_fp64_2d_config1_1000_2000_steps(T, O):
     assert np.abs(fg - fo).max() < 1e-12 and np.abs(gg - go).max() < 1e-12
 
 
-def test_fp64_3d_parity(T, O):
-    """D3Q19 + D3Q7 cube, 500 steps (walls on every face)."""
+@pytest.mark.parametrize("kw", [{}, {"streaming": 1}], ids=["pull", "inplace"])
+def test_fp64_3d_parity(T, O, kw):
+    """D3Q19 + D3Q7 cube, 500 steps (walls on every face), both streaming schemes."""
     n = 33
-    g = T.Sim(n, n, n, lattice=D3, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64)
+    g = T.Sim(n, n, n, lattice=D3, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64, **kw)
     o = O.Sim(n, n, n, lattice=D3, Ra=1e5, Pr=0.71, Ma=0.1)
     O.set_threads(8)
     g.init(3, 1e-3)
