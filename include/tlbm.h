@@ -248,8 +248,8 @@ TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bloc
  * thread and write the results back in place, and the tile leaves with bulk
  * copies shared -> global; `stages` tiles are in flight per block.
  * tile_width: a multiple of 16 bytes' worth of elements, at most 512 (0 =
- * whole rows up to 512 nodes, else 512); stages: 3 .. 8 (0 = the most that leave
- * two blocks per SM).  FP32/FP16/BF16 storage with two-relaxation-time rates
+ * whole rows up to 512 nodes, else 512); stages: 2 .. 8 (0 = the most tiles in
+ * flight per SM, blocks x stages, up to six, more blocks first).  FP32/FP16/BF16 storage with two-relaxation-time rates
  * only (TLBM_ERR_UNSUPPORTED otherwise).  A block that waits too long for its
  * copies gives up; the next synchronising call then returns TLBM_ERR_TIMEOUT.
  * tlbm_set_variant switches back to the register kernels. */

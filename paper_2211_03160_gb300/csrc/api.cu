@@ -713,10 +713,11 @@ extern "C" int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes) {
 #endif
     set_cur(h, 0);
     // 2D FP16/BF16 storage with two-relaxation-time rates defaults to the
-    // shared-memory staged kernel (512-node tiles, 3 stages: the fastest on
-    // GB300); the register kernel stays if the device cannot host it
+    // shared-memory staged kernel (512-node tiles, stages chosen as above: 2
+    // stages and three blocks per SM on GB300, the fastest there); the register
+    // kernel stays if the device cannot host it
     if (!h->variant_chosen && !h->aa && h->dim == 2 && (h->prec == TLBM_FP16_OFFSET || h->prec == TLBM_BF16_OFFSET) &&
-        h->kp.trt && set_staged(h, 512, 3) != TLBM_OK) {
+        h->kp.trt && set_staged(h, 512, 0) != TLBM_OK) {
         h->staged = 0;
         h->err[0] = 0;
     }
@@ -1220,20 +1221,27 @@ static int set_staged(tlbm_t h, int tile_width, int stages) {
     const int threads = 32 * (nc + 1);
     int ns = stages;
     if (ns <= 0) {
-        // the most stages that still leave two blocks per SM, else the most for one
-        ns = 0;
-        for (int want = 2; want >= 1 && ns == 0; --want)
-            for (int k = TILE_MAX_STAGES; k >= 2; --k) {
-                int b = 0;
-                const size_t sm = 512 + (size_t)k * stage_bytes;
-                if (sm > (size_t)optin) continue;
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, sm);
-                if (e != cudaSuccess) return cuda_fail(h, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-                if (b >= want) {
-                    ns = k;
-                    break;
-                }
+        // the most tiles in flight per SM (blocks per SM x stages) up to six,
+        // more blocks first (else the fewest stages that fit): on GB300 2 x 3
+        // was best for 96-register consumers, 3 x 2 for 72-register ones, and
+        // more in flight was slower
+        int first = 0, best_in = 0, best_b = 0;
+        for (int k = 2; k <= TILE_MAX_STAGES; ++k) {
+            int b = 0;
+            const size_t sm = 512 + (size_t)k * stage_bytes;
+            if (sm > (size_t)optin) break;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, sm);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+            if (b < 1) break;
+            if (!first) first = k;
+            const int in = b * k;
+            if (in <= 6 && (in > best_in || (in == best_in && b > best_b))) {
+                ns = k;
+                best_in = in;
+                best_b = b;
             }
+        }
+        if (ns == 0) ns = first;
         if (ns == 0) return fail(h, TLBM_ERR_ARG, "two stages of %zu bytes do not fit in shared memory", stage_bytes);
     }
     if (ns < 2 || ns > TILE_MAX_STAGES) return fail(h, TLBM_ERR_ARG, "stages must be in [2, %d]", TILE_MAX_STAGES);

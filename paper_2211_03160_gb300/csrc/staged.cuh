@@ -136,8 +136,12 @@ struct TileGeo {
     static constexpr int LW = TWMAX + 2 * A;
 };
 
+// Register caps: the 2D instance with 8 consumer warps fits in 72 registers
+// without spilling, which leaves room for three blocks per SM (27 warps); with
+// two stages each that measured 114.8 GLUPS at 8193^2 FP16 against 113.1 for
+// two blocks of 96 registers with three stages (GB300, same box).
 template <int DIM, class S, int NC>
-__global__ void __maxnreg__(NC == 8 ? 112 : 168)
+__global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 112 : 168))
     step_staged_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p, const StagedInfo si) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
