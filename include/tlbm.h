@@ -270,6 +270,10 @@ TLBM_API int tlbm_set_wait_limit(tlbm_t h, double seconds);
  * covers everything since tlbm_bind_memory.  Synchronises.  The release
  * library returns TLBM_ERR_UNSUPPORTED. */
 TLBM_API int tlbm_bounds_violations(tlbm_t h, int64_t* count);
+/* The staged kernel's configuration as chosen (all 0 when the register kernels
+ * are in use): tile width in nodes, stages per block, and the persistent grid
+ * (blocks per SM x SMs).  Outputs may be NULL. */
+TLBM_API int tlbm_get_staged(tlbm_t h, int* tile_width, int* stages, int* blocks);
 /* Current variant (form reported as 1 MRT or 2 TRT; vec 0 for the staged
  * kernel).  Outputs may be NULL. */
 TLBM_API int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y, int* rows);

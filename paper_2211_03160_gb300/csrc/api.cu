@@ -1277,6 +1277,14 @@ extern "C" int tlbm_set_wait_limit(tlbm_t h, double seconds) {
     return TLBM_OK;
 }
 
+extern "C" int tlbm_get_staged(tlbm_t h, int* tile_width, int* stages, int* blocks) {
+    TLBM_CHECK_HANDLE(h);
+    if (tile_width) *tile_width = h->staged ? h->staged_tw : 0;
+    if (stages) *stages = h->staged ? h->staged_stages : 0;
+    if (blocks) *blocks = h->staged ? h->staged_grid : 0;
+    return TLBM_OK;
+}
+
 extern "C" int tlbm_get_variant(tlbm_t h, int* vec, int* form, int* block_x, int* block_y, int* rows) {
     TLBM_CHECK_HANDLE(h);
     if (rows) *rows = h->rows;

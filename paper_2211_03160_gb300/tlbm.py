@@ -81,6 +81,7 @@ _SIGS = {
     "tlbm_get_variant": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "tlbm_get_staged": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "tlbm_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "tlbm_bounds_violations": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "tlbm_load": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -341,6 +342,13 @@ def tlbm_set_staged(h, tile_width=0, stages=0):
     _check(h, lib().tlbm_set_staged(h, int(tile_width), int(stages)))
 
 
+def tlbm_get_staged(h):
+    """(tile width, stages, blocks) of the staged kernel, zeros for the register kernels."""
+    tw, ns, nb = C.c_int(), C.c_int(), C.c_int()
+    _check(h, lib().tlbm_get_staged(h, C.byref(tw), C.byref(ns), C.byref(nb)))
+    return tw.value, ns.value, nb.value
+
+
 def tlbm_set_wait_limit(h, seconds):
     _check(h, lib().tlbm_set_wait_limit(h, float(seconds)))
 
@@ -511,6 +519,10 @@ class Sim:
     @property
     def variant(self):
         return tlbm_get_variant(self.h)
+
+    @property
+    def staged(self):
+        return tlbm_get_staged(self.h)
 
     @property
     def launches(self):

@@ -366,6 +366,22 @@ def test_staged_at_bench_size(T):
     assert all(np.array_equal(a, b) for a, b in zip(outs[0] + outs[1], outs[2] + outs[3]))
 
 
+def test_staged_default_configuration(T):
+    """2D FP16/BF16 default to the staged kernel with 512-node tiles and the
+    stage count that keeps at most six tiles in flight per SM; tlbm_get_staged
+    reports it, and the register kernels report zeros."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for prec in (FP16, BF16):
+        g = T.Sim(1025, 257, lattice=D2, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
+        tw, ns, nb = g.staged
+        assert tw == 512 and 2 <= ns <= 8 and nb % sms == 0 and (nb // sms) * ns <= 6, (tw, ns, nb)
+        g.set_variant(4, 2, 32, 1, 1)
+        assert g.staged == (0, 0, 0)
+        g.close()
+
+
 def test_launch_count(T):
     g = T.Sim(64, 64, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP32)
     g.init(1, 0.0)
