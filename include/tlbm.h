@@ -320,8 +320,17 @@ TLBM_API int tlbm_batch_set_persistent(tlbm_batch_t b, int steps_per_launch);
 TLBM_API int tlbm_batch_set_wait_limit(tlbm_batch_t b, double seconds);
 TLBM_API int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* block_x, int* block_y,
                                     int* graph_steps);
-/* Time the compiled launch shapes (trials launches each) on the bound state and
- * keep the fastest.  The state is not changed. */
+/* Rows per thread of the flattened launch: 1, or 2 (the software-pipelined
+ * body: the next row's loads are issued before the current row is collided;
+ * two-relaxation-time rates, TLBM_ERR_UNSUPPORTED where not compiled).  The
+ * persistent form always runs one row per thread.  tlbm_batch_set_variant
+ * falls back to 1 for a vector width without the 2-row variant;
+ * tlbm_batch_autotune tries both. */
+TLBM_API int tlbm_batch_set_rows(tlbm_batch_t b, int rows);
+TLBM_API int tlbm_batch_get_rows(tlbm_batch_t b, int* rows);
+/* Time the compiled launch shapes (nodes per thread x rows per thread x block
+ * shape, trials launches each) on the bound state and keep the fastest.  The
+ * state is not changed. */
 TLBM_API int tlbm_batch_autotune(tlbm_batch_t b, int trials);
 /* (trials < 0: reuse the shape this process tuned for the same lattice, storage,
  * collision form and size class floor(log2(total nodes)), if any.) */

@@ -35,8 +35,9 @@ struct BatchInst {
 // Tile b of the flattened grid belongs to the instance i with
 // block0[i] <= b < block0[i+1]; its parameters are staged in shared memory.
 // Called by all threads of a block together.  CG: the loads bypass L1 (the
-// persistent kernel reads what other blocks wrote in the previous step).
-template <int DIM, class S, int VEC, bool TRT, bool CG = false>
+// persistent kernel reads what other blocks wrote in the previous step).  ROWS
+// > 1: the software-pipelined body (ROWS rows per thread; flattened form only).
+template <int DIM, class S, int VEC, bool TRT, bool CG = false, int ROWS = 1>
 __device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
                                            int parity, long long b, KParams& sp, int& si) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -64,15 +65,20 @@ __device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, cons
     const long long r = local / in.gx;
     const int by = (int)(r % in.gy);
     const int bz = (int)(r / in.gy);
-    step_block<DIM, S, VEC, TRT, CG>((const S*)in.buf[parity], (S*)in.buf[parity ^ 1], sp, bx, by, bz);
+    if constexpr (ROWS > 1) {
+        static_assert(!CG, "the pipelined body reads through L1");
+        step_rows_block<DIM, S, VEC, TRT, ROWS>((const S*)in.buf[parity], (S*)in.buf[parity ^ 1], sp, bx, by, bz);
+    } else {
+        step_block<DIM, S, VEC, TRT, CG>((const S*)in.buf[parity], (S*)in.buf[parity ^ 1], sp, bx, by, bz);
+    }
 }
 
-template <int DIM, class S, int VEC, bool TRT>
+template <int DIM, class S, int VEC, bool TRT, int ROWS = 1>
 __global__ void batch_step_kernel(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
                                   int parity) {
     __shared__ KParams sp;
     __shared__ int si;
-    batch_tile<DIM, S, VEC, TRT>(kps, inst, n, parity, blockIdx.x, sp, si);
+    batch_tile<DIM, S, VEC, TRT, false, ROWS>(kps, inst, n, parity, blockIdx.x, sp, si);
 }
 
 // ------------------------------------------------------------------ persistent form
@@ -157,7 +163,7 @@ struct Persist {
 };
 
 #define TLBM_BATCH_CASE(DIM, S, PREC, VEC, TRT)                                                      \
-    if (dim == DIM && prec == PREC && vec == VEC && trt == TRT) {                                   \
+    if (dim == DIM && prec == PREC && vec == VEC && trt == TRT && rows == 1) {                      \
         if (pp && pp->per_sm_out)                                                                   \
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                   \
                 pp->per_sm_out, batch_persistent_kernel<DIM, S, VEC, TRT>, block.x * block.y, 0);    \
@@ -178,9 +184,26 @@ struct Persist {
         return launch ? cudaGetLastError() : cudaSuccess;                                           \
     }
 
+// pipelined rows (flattened form, two-relaxation-time collision)
+#define TLBM_BATCH_ROWS_CASE(DIM, S, PREC, VEC, ROWS)                                                  \
+    if (dim == DIM && prec == PREC && vec == VEC && trt && rows == ROWS) {                           \
+        if (pp) return cudaErrorInvalidValue;                                                         \
+        if (launch)                                                                                   \
+            batch_step_kernel<DIM, S, VEC, true, ROWS><<<grid, block, 0, s>>>(kps, inst, n, parity);  \
+        return launch ? cudaGetLastError() : cudaSuccess;                                             \
+    }
+
 cudaError_t batch_dispatch(bool launch, int dim, int prec, int vec, bool trt, const KParams* kps,
                            const BatchInst* inst, int n, int parity, long long grid, dim3 block, cudaStream_t s,
-                           const Persist* pp = nullptr) {
+                           const Persist* pp = nullptr, int rows = 1) {
+    TLBM_BATCH_ROWS_CASE(2, float, 1, 4, 2)
+    TLBM_BATCH_ROWS_CASE(2, __half, 2, 4, 2)
+    TLBM_BATCH_ROWS_CASE(2, __half, 2, 8, 2)
+    TLBM_BATCH_ROWS_CASE(2, __nv_bfloat16, 3, 4, 2)
+    TLBM_BATCH_ROWS_CASE(2, __nv_bfloat16, 3, 8, 2)
+    TLBM_BATCH_ROWS_CASE(3, float, 1, 1, 2)
+    TLBM_BATCH_ROWS_CASE(3, __half, 2, 1, 2)
+    TLBM_BATCH_ROWS_CASE(3, __nv_bfloat16, 3, 1, 2)
     TLBM_BATCH_CASE(2, float, 1, 4, true)
     TLBM_BATCH_CASE(2, float, 1, 2, true)
     TLBM_BATCH_CASE(2, float, 1, 4, false)
@@ -222,6 +245,7 @@ struct tlbm_batch_s {
     BatchInst* d_inst;
     GridSync* d_sync;
     int vec, trt, bx, by;
+    int rows;           // rows per thread of the flattened launch (1 or 2)
     int graph_steps;
     int persist_steps;  // > 0: persistent kernel, this many steps per launch
     unsigned long long wait_ns;  // grid-barrier wait limit of the persistent kernel
@@ -274,6 +298,9 @@ static void batch_default_variant(tlbm_batch_t b) {
     }
 }
 
+// rows per thread of the tables and launches: the persistent form runs one
+static int eff_rows(tlbm_batch_t b) { return b->persist_steps > 0 ? 1 : b->rows; }
+
 // per-instance tables for the flattened launch (host side)
 static void build_tables(tlbm_batch_t b, std::vector<KParams>& kps, std::vector<BatchInst>& ins) {
     kps.resize(b->n);
@@ -285,7 +312,8 @@ static void build_tables(tlbm_batch_t b, std::vector<KParams>& kps, std::vector<
         kps[i].xmax_load = h->kp.L.P - b->vec;
         const int tx = (h->nx + b->vec - 1) / b->vec;
         const int gx = (tx + b->bx - 1) / b->bx;
-        const int gy = (h->ny + b->by - 1) / b->by;
+        const int rows = eff_rows(b);
+        const int gy = (h->ny + b->by * rows - 1) / (b->by * rows);
         ins[i].buf[0] = h->buf[0];
         ins[i].buf[1] = h->buf[1];
         ins[i].block0 = block0;
@@ -311,7 +339,7 @@ static int upload_tables(tlbm_batch_t b) {
 
 static cudaError_t launch_batch(tlbm_batch_t b, int parity, cudaStream_t s) {
     return batch_dispatch(true, b->dim, b->prec, b->vec, b->trt != 0, b->d_kp, b->d_inst, b->n, parity,
-                          b->total_blocks, dim3(b->bx, b->by, 1), s);
+                          b->total_blocks, dim3(b->bx, b->by, 1), s, nullptr, eff_rows(b));
 }
 
 extern "C" int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* instances, int lattice,
@@ -329,6 +357,7 @@ extern "C" int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* 
     b->prec = precision;
     b->dim = lattice == TLBM_D3Q19_D3Q7 ? 3 : 2;
     b->graph_steps = 16;
+    b->rows = 1;
     b->wait_ns = GRID_WAIT_NS;
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
@@ -514,6 +543,9 @@ extern "C" int tlbm_batch_set_variant(tlbm_batch_t b, int vec, int form, int blo
     b->bx = bx;
     b->by = by;
     b->graph_steps = graph_steps;
+    if (batch_dispatch(false, b->dim, b->prec, v, trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr, nullptr, b->rows) !=
+        cudaSuccess)
+        b->rows = 1;  // no pipelined-row variant for this one
     if (b->mem) return upload_tables(b);
     return TLBM_OK;
 }
@@ -528,6 +560,25 @@ extern "C" int tlbm_batch_set_persistent(tlbm_batch_t b, int steps_per_launch) {
     if (steps_per_launch > 0 && (e != cudaSuccess || !coop))
         return bfail(b, TLBM_ERR_UNSUPPORTED, "the device has no cooperative launch");
     b->persist_steps = steps_per_launch;
+    if (b->mem) return upload_tables(b);  // the persistent form runs one row per thread
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_set_rows(tlbm_batch_t b, int rows) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (rows != 1 && rows != 2) return bfail(b, TLBM_ERR_ARG, "rows must be 1 or 2");
+    if (batch_dispatch(false, b->dim, b->prec, b->vec, b->trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr, nullptr, rows) !=
+        cudaSuccess)
+        return bfail(b, TLBM_ERR_UNSUPPORTED, "batch variant (vec %d, %d rows) not built", b->vec, rows);
+    b->rows = rows;
+    if (b->mem) return upload_tables(b);
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_get_rows(tlbm_batch_t b, int* rows) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (!rows) return bfail(b, TLBM_ERR_ARG, "rows is NULL");
+    *rows = b->rows;
     return TLBM_OK;
 }
 
@@ -545,7 +596,7 @@ extern "C" int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* 
 // Tuned launch shapes of this process, per (lattice, storage, collision form,
 // size class = floor(log2(total nodes))).
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int>, std::array<int, 3>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int>, std::array<int, 4>> g_tune_cache;
 
 static std::tuple<int, int, int, int> tune_key(tlbm_batch_t b) {
     long long nodes = 0;
@@ -570,25 +621,30 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
             b->vec = it->second[0];
             b->bx = it->second[1];
             b->by = it->second[2];
+            b->rows = it->second[3];
             return upload_tables(b);
         }
     }
     const int reps = trials > 0 ? trials : 5;
     const int vecs[] = {8, 4, 2, 1};
     const int shapes[][2] = {{32, 1}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}};
-    const int keep_vec = b->vec, keep_bx = b->bx, keep_by = b->by;
+    const int keep_vec = b->vec, keep_bx = b->bx, keep_by = b->by, keep_rows = b->rows;
     float best = 1e30f;
-    int bv = keep_vec, bbx = keep_bx, bby = keep_by;
+    int bv = keep_vec, bbx = keep_bx, bby = keep_by, brows = keep_rows;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, TLBM_ERR_CUDA, "cudaEventCreate");
     int rc = TLBM_OK;
-    for (int v : vecs) {
-        if (batch_dispatch(false, b->dim, b->prec, v, b->trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr) !=
+    // rows per thread: the persistent form runs one
+    const int max_rows = b->persist_steps > 0 ? 1 : 2;
+    for (int v : vecs)
+    for (int nr = 1; nr <= max_rows; ++nr) {
+        if (batch_dispatch(false, b->dim, b->prec, v, b->trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr, nullptr, nr) !=
             cudaSuccess)
             continue;
         for (const auto& sh : shapes) {
             b->vec = v;
+            b->rows = nr;
             b->bx = sh[0];
             b->by = sh[1];
             if ((rc = upload_tables(b)) != TLBM_OK) break;
@@ -608,6 +664,7 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
             if (ms < best) {
                 best = ms;
                 bv = v;
+                brows = nr;
                 bbx = sh[0];
                 bby = sh[1];
             }
@@ -617,11 +674,12 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->vec = bv;
+    b->rows = brows;
     b->bx = bbx;
     b->by = bby;
     if (rc == TLBM_OK) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[tune_key(b)] = {bv, bbx, bby};
+        g_tune_cache[tune_key(b)] = {bv, bbx, bby, brows};
     }
     int rc2 = upload_tables(b);
     return rc != TLBM_OK ? rc : rc2;

@@ -1362,17 +1362,19 @@ __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p
 // ROWS consecutive rows per thread, software-pipelined: the loads of the next
 // row are issued before the current row is collided, so every warp keeps loads
 // in flight while it computes.
+// Body of the software-pipelined kernel for the block at grid position (bx, by, bz).
 template <int DIM, class S, int VEC, bool TRT, int ROWS>
-__global__ void step_kernel_rows(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
+__device__ __forceinline__ void step_rows_block(const S* __restrict__ src, S* __restrict__ dst, const KParams& p,
+                                                int bx, int by, int bz) {
     using C = typename Storage<S>::C;
     constexpr int QF = Lat<DIM>::F::Q, QG = Lat<DIM>::G::Q;
     constexpr bool KS = TRT && Storage<S>::offset;
     const Layout& L = p.L;
     const int lane = threadIdx.x & 31;
-    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * ROWS;
-    const int z = DIM == 3 ? (int)blockIdx.z : 0;
+    const int y0 = (by * blockDim.y + threadIdx.y) * ROWS;
+    const int z = DIM == 3 ? bz : 0;
     if (y0 >= L.ny) return;  // uniform across the warp
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
+    const int x0 = (bx * blockDim.x + threadIdx.x) * VEC;
     if (x0 - lane * VEC >= L.nx) return;  // the whole warp lies past the row end
     const int x0ld = min(x0, p.xmax_load);
     const long long row0 = L.row(y0, z);
@@ -1397,6 +1399,11 @@ __global__ void step_kernel_rows(const S* __restrict__ src, S* __restrict__ dst,
         }
         if (yb + 1 >= L.ny) break;
     }
+}
+
+template <int DIM, class S, int VEC, bool TRT, int ROWS>
+__global__ void step_kernel_rows(const S* __restrict__ src, S* __restrict__ dst, const KParams p) {
+    step_rows_block<DIM, S, VEC, TRT, ROWS>(src, dst, p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int DIM, class S, int VEC, bool TRT>

@@ -81,6 +81,8 @@ _SIGS = {
     "tlbm_get_variant": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
     "tlbm_reduce_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "tlbm_batch_set_rows": (C.c_int, [C.c_void_p, C.c_int]),
+    "tlbm_batch_get_rows": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "tlbm_get_staged": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "tlbm_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "tlbm_bounds_violations": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
@@ -590,6 +592,16 @@ def tlbm_batch_set_persistent(b, steps_per_launch: int):
     _bcheck(b, lib().tlbm_batch_set_persistent(b, int(steps_per_launch)))
 
 
+def tlbm_batch_set_rows(b, rows: int):
+    _bcheck(b, lib().tlbm_batch_set_rows(b, int(rows)))
+
+
+def tlbm_batch_get_rows(b) -> int:
+    r = C.c_int()
+    _bcheck(b, lib().tlbm_batch_get_rows(b, C.byref(r)))
+    return r.value
+
+
 def tlbm_batch_set_wait_limit(b, seconds):
     _bcheck(b, lib().tlbm_batch_set_wait_limit(b, float(seconds)))
 
@@ -683,6 +695,13 @@ class Batch:
 
     def set_persistent(self, steps_per_launch):
         tlbm_batch_set_persistent(self.b, steps_per_launch)
+
+    def set_rows(self, rows):
+        tlbm_batch_set_rows(self.b, rows)
+
+    @property
+    def rows(self):
+        return tlbm_batch_get_rows(self.b)
 
     def set_wait_limit(self, seconds):
         tlbm_batch_set_wait_limit(self.b, seconds)

@@ -143,3 +143,34 @@ def test_autotune_cache_reuses_the_tuned_shape(T):
     assert b.variant[:4] == tuned and b.launches == l0
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("lattice,prec", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2)])
+def test_batch_pipelined_rows_equal_one_row(T, lattice, prec):
+    """Two rows per thread (software-pipelined body) in the flattened batch
+    launch give bitwise the states of one row per thread, for odd row counts
+    and step counts spanning a graph block; the persistent form switches back to
+    one row and still agrees."""
+    inst = _draws(5, (33, 65, 97), seed=6, lattice=lattice)
+    a = T.Batch(inst, lattice=lattice, precision=prec)
+    b = T.Batch(inst, lattice=lattice, precision=prec)
+    vec = {(0, 1): 4, (0, 2): 8, (0, 3): 4, (1, 1): 1, (1, 2): 1}[(lattice, prec)]
+    for x in (a, b):
+        x.set_variant(vec, 2, 32, 2, 16)
+    a.set_rows(1)
+    b.set_rows(2)
+    assert (a.rows, b.rows) == (1, 2)
+    for x in (a, b):
+        x.init(1e-3)
+        x.step(37)
+    for k in range(len(inst)):
+        (fa, ga), (fb, gb) = a.get_populations(k), b.get_populations(k)
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), k
+    b.set_persistent(8)
+    for x in (a, b):
+        x.step(16)
+    for k in range(len(inst)):
+        (fa, ga), (fb, gb) = a.get_populations(k), b.get_populations(k)
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), k
+    a.close()
+    b.close()
