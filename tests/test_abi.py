@@ -206,3 +206,22 @@ def test_checkpoint_needs_bound_memory_and_a_path(T):
             assert fn(h, None) == T.TLBM_ERR_UNBOUND
     finally:
         T.tlbm_destroy(h)
+
+
+def test_staged_query_and_batch_rows_on_host(T):
+    h = T.tlbm_create(33, 17, 1, 0, 1e5, 0.71, 0.1, 2)
+    try:
+        assert T.tlbm_get_staged(h) == (0, 0, 0)  # not bound: the register kernels
+    finally:
+        T.tlbm_destroy(h)
+    b = T.tlbm_batch_create([(33, 33, 1, 1e5, 0.71, 0.1, 1)], 0, 1)
+    try:
+        assert T.tlbm_batch_get_rows(b) == 1
+        for bad in (0, 3, -1):
+            with pytest.raises(T.TlbmError) as ei:
+                T.tlbm_batch_set_rows(b, bad)
+            assert ei.value.code == T.TLBM_ERR_ARG
+        T.tlbm_batch_set_rows(b, 2)
+        assert T.tlbm_batch_get_rows(b) == 2
+    finally:
+        T.tlbm_batch_destroy(b)
