@@ -42,7 +42,20 @@ __device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, cons
                                            int parity, long long b, KParams& sp, int& si) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nt = blockDim.x * blockDim.y;
-    if (tid == 0) {
+    if (n <= 128) {
+        // warp 0: the instances with block0 <= b, counted by ballot (block0 rises
+        // with the instance index), all lanes' loads in flight at once
+        if (tid < 32) {
+            int count = 0;
+#pragma unroll
+            for (int base = 0; base < 128; base += 32) {
+                const int k = base + tid;
+                const bool le = k < n && inst[k].block0 <= b;
+                count += __popc(__ballot_sync(0xffffffffu, le));
+            }
+            if (tid == 0) si = count - 1;
+        }
+    } else if (tid == 0) {
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) / 2;
@@ -54,9 +67,10 @@ __device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, cons
     __syncthreads();
     const int i = si;
     {
-        const int* src = reinterpret_cast<const int*>(kps + i);
-        int* dst = reinterpret_cast<int*>(&sp);
-        for (int w = tid; w < (int)(sizeof(KParams) / sizeof(int)); w += nt) dst[w] = src[w];
+        static_assert(sizeof(KParams) % sizeof(long long) == 0, "KParams copied in 8-byte words");
+        const long long* src = reinterpret_cast<const long long*>(kps + i);
+        long long* dst = reinterpret_cast<long long*>(&sp);
+        for (int w = tid; w < (int)(sizeof(KParams) / sizeof(long long)); w += nt) dst[w] = src[w];
     }
     __syncthreads();
     const BatchInst in = inst[i];
