@@ -15,6 +15,7 @@ import pytest
 
 import test_oracle_algebra as A
 import test_oracle_bruteforce as B
+import test_oracle_diagnostics as Dg
 import test_oracle_physics as Ph
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -35,6 +36,9 @@ MUTANTS = {
     "diffusivity_mapping": ("double qj = 1.0 / (s->alpha / s->omega + 0.5);",
                             "double qj = 1.0 / (s->alpha / s->omega + 1.0);"),
     "d3q19_row": ("case 4: return (5.0 * e2 - 9.0) * ex;", "case 4: return (5.0 * e2 - 8.0) * ex;"),
+    "energy_half": ("e += 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);",
+                    "e += r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);"),
+    "mass_sum": ("m += r;", "m += t;"),
     "nusselt_scale": ("return 1.0 + L * (sum / (double)s->N) / (s->alpha * dT);",
                       "return 1.0 + 0.5 * L * (sum / (double)s->N) / (s->alpha * dT);"),
 }
@@ -60,6 +64,7 @@ def _pins(O):
         lambda: B.test_one_step_pull_equals_push(O, 1, (5, 4, 3), 0, 0),
         lambda: Ph.test_buoyancy_enters_the_velocity_along_gravity(O, 0, (9, 12, 1)),
         lambda: Ph.test_nusselt_of_a_uniform_flow(O, 0),
+        lambda: Dg.test_energy_and_mass_of_a_given_state(O, 0, (23, 17, 1)),
     ]
 
 
