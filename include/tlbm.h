@@ -398,14 +398,20 @@ TLBM_API int tlbm_upsample_bilinear(const float* in, int channels, int h, int w,
 /* FP64 diagnostic sums of a population state without any device memory from
  * the caller beyond the state itself (the paper has no counterpart; this is a
  * library service).  For callers that hold a state but cannot allocate device
- * memory, e.g. a process that maps another process's state through CUDA IPC on
- * a GPU where it may not allocate, or code running while another thread holds
- * a global-mode stream capture (cudaMalloc is refused until it ends).
- *   h:     handle describing the cell, precision and parameters; it needs bound
- *          memory only when state is NULL.
+ * memory: e.g. a monitoring process that maps a running simulation's state
+ * through CUDA IPC on a GPU whose memory that simulation has taken, or an
+ * application whose device memory is all held by its own pool allocator, so
+ * that the scratch block of tlbm_bind_memory cannot be had.
+ *   h:     handle describing the cell, precision, streaming scheme and
+ *          parameters; it needs bound memory only when state is NULL.
  *   state: device pointer to a population buffer laid out as described at
  *          tlbm_bind_memory for a handle created with the same arguments, or
- *          NULL for h's current state.
+ *          NULL for h's current state.  It is read in the storage order of h's
+ *          own current state: the pull layout for two-buffer handles; for
+ *          in-place handles (TLBM_STREAM_INPLACE) the natural order when h has
+ *          taken an even number of steps (a fresh handle included) and the
+ *          swapped order after an odd number.  A state in the other order gives
+ *          wrong sums without an error.
  *   out:   host array of 6 doubles: sum u_h T, sum 1/2 rho |u|^2, sum rho,
  *          max |u|^2, non-finite flag (1.0 if any), sum T; u_h as in tlbm_nusselt.
  * The block partial sums live in a static device array compiled into the

@@ -5,9 +5,9 @@
 // The handle-based reductions keep their block partials in the scratch part of
 // the block the caller bound with tlbm_bind_memory.  Some callers hold a
 // population state but cannot allocate any device memory to go with it: for
-// example a process that maps another process's state through CUDA IPC on a
-// GPU where it may not allocate, or code that runs while another thread holds
-// a global-mode stream capture (cudaMalloc is refused until that capture ends).
+// example a monitoring process that maps a running simulation's state through
+// CUDA IPC on a GPU whose memory that simulation has taken, or an application
+// whose device memory is all held by its own pool allocator.
 // This entry point needs nothing from them but the state and a host array: its
 // partial sums live in a fixed array compiled into this file, and nothing here
 // calls cudaMalloc, cudaFree or any allocating routine.

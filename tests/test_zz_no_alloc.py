@@ -101,3 +101,49 @@ def test_noalloc_flags_divergence(T):
     sim.set_populations(f, g)
     s = T.tlbm_reduce_noalloc(sim.h)
     assert s[3] > 0.25 and sim.status()[0]
+
+
+def test_noalloc_in_place_state_order(T):
+    """In-place streaming keeps the state in natural order after an even number
+    of steps and in swapped order after an odd number; a state passed by pointer
+    is read in the order of the handle's own current state."""
+    shape = (131, 67, 1)
+    sim = T.Sim(*shape, lattice=0, Ra=1e6, Pr=0.71, Ma=0.1, precision=1, streaming=T.TLBM_STREAM_INPLACE)
+    sim.init(5, 1e-3)
+    sim.step(11)  # odd: swapped order
+    own = T.tlbm_reduce_noalloc(sim.h, sim.mem.data_ptr())
+    _check_against_handle_path(T, sim, own)
+    assert own == T.tlbm_reduce_noalloc(sim.h)
+    sim.step(1)  # even: natural order, as a fresh handle reads it
+    ref = T.tlbm_reduce_noalloc(sim.h)
+    _check_against_handle_path(T, sim, ref)
+    params = T.tlbm_default_params(streaming=T.TLBM_STREAM_INPLACE)
+    h = T.tlbm_create(*shape, 0, 1e6, 0.71, 0.1, 1, params)
+    try:
+        a = T.tlbm_reduce_noalloc(h, sim.mem.data_ptr())
+        b = T.tlbm_reduce_noalloc(h, sim.mem.data_ptr())
+    finally:
+        T.tlbm_destroy(h)
+    assert a == ref and b == ref
+
+
+def test_noalloc_call_allocates_no_device_memory(T):
+    """After the first call on the device (which looks up the static array's
+    address), further calls leave the device's free memory and torch's
+    allocator untouched."""
+    import torch
+
+    sim = T.Sim(513, 257, lattice=0, Ra=1e7, Pr=0.71, Ma=0.1, precision=2)
+    sim.init(6, 1e-3)
+    sim.step(4)
+    first = T.tlbm_reduce_noalloc(sim.h)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    again = [T.tlbm_reduce_noalloc(sim.h) for _ in range(3)]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    assert stats1.get("allocation.all.allocated", 0) == stats0.get("allocation.all.allocated", 0)
+    assert all(a == first for a in again)
