@@ -41,6 +41,12 @@ METRIC = ("GLUPS & % HBM roofline, 8193² D2Q9+D2Q5 / 385³ D3Q19+D3Q7, "
 # algorithmic bytes per lattice update: every population read once, written once
 BYTES_PER_LU = {(2, "fp64"): 224, (2, "fp32"): 112, (2, "fp16"): 56, (2, "bf16"): 56,
                 (3, "fp64"): 416, (3, "fp32"): 208, (3, "fp16"): 104, (3, "bf16"): 104}
+# FP64 operations the FP64 storage step executes per lattice update (ncu:
+# smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on per node on
+# 1025^2 / 129^3; FLOP counts a DFMA as 2).  The FP64 build is compiled without
+# FMA contraction (oracle parity to 1e-12), so nearly every operation is its own
+# FP64 instruction: the roof of that mix is the FP64 pipe's instruction rate.
+FP64_OPS_PER_LU = {2: {"dadd": 121.5, "dmul": 90.8, "dfma": 5.3}, 3: {"dadd": 288.2, "dmul": 193.5, "dfma": 6.2}}
 KERNEL_SOURCES = ["paper_2211_03160_gb300/csrc/kernels.cuh", "paper_2211_03160_gb300/csrc/lattice.cuh",
                   "paper_2211_03160_gb300/csrc/dispatch.h", "paper_2211_03160_gb300/csrc/step_2d_f32.cu",
                   "paper_2211_03160_gb300/csrc/step_2d_f16.cu", "paper_2211_03160_gb300/csrc/step_3d_f32.cu",
@@ -184,8 +190,10 @@ def workload(name: str):
         "2d_8193_fp16": (2, 8193, 8193, 1, 1e8, "fp16", 2),
         "2d_8193_bf16": (2, 8193, 8193, 1, 1e8, "bf16", 2),
         "2d_8193_fp64": (2, 8193, 8193, 1, 1e8, "fp64", 2),
+        "3d_385_fp64": (3, 385, 385, 385, 1e7, "fp64", 3),
         "3d_385_fp32": (3, 385, 385, 385, 1e7, "fp32", 3),
         "3d_385_fp16": (3, 385, 385, 385, 1e7, "fp16", 3),
+        "3d_385_bf16": (3, 385, 385, 385, 1e7, "bf16", 3),
         # smaller cases of the same physics for profiler captures (still > L2)
         "2d_4097_fp32": (2, 4097, 4097, 1, 1e8, "fp32", 2),
         "2d_4097_fp16": (2, 4097, 4097, 1, 1e8, "fp16", 2),
@@ -368,6 +376,19 @@ def run_batch(prec: str, steps: int, warmup: int, ws: int, device_index: int) ->
     return out
 
 
+_FP64_PEAK = None
+
+
+def fp64_peak() -> float:
+    """Measured FP64 FMA rate of this GPU (FLOP/s), taken once per run."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        from paper_2211_03160_gb300 import tlbm
+
+        _FP64_PEAK = tlbm.tlbm_fp64_fma_rate()
+    return _FP64_PEAK
+
+
 def cpu_baseline(target_seconds: float = 12.0) -> dict:
     """The FP64 oracle as it stands on the host cores (OpenMP over all cores),
     on a bounded sample of the headline workload: the same physics (Ra = 1e8,
@@ -480,9 +501,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d_8193_fp32")
-    ap.add_argument("--variants", default="2d_8193_fp16,2d_8193_bf16,3d_385_fp32,3d_385_fp16,2d_8193_fp64,"
-                                          "2d_8193_fp32_inplace,3d_385_fp16_inplace,2d_8193_fp32_side,"
-                                          "batch64_fp32,batch64_fp16")
+    ap.add_argument("--variants", default="2d_8193_fp16,2d_8193_bf16,3d_385_fp32,3d_385_fp16,3d_385_bf16,"
+                                          "2d_8193_fp64,3d_385_fp64,2d_8193_fp32_inplace,3d_385_fp16_inplace,"
+                                          "2d_8193_fp32_side,batch64_fp32,batch64_fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-full", action="store_true",
@@ -511,31 +532,39 @@ def main():
             st = max(10, args.steps // 4)
             r = run_batch(v.split("_")[1], st, min(args.warmup, 20), ws, local)
             bt, sp = r["batched"], r["separate"]
+            bpl = BYTES_PER_LU[(2, r["prec"])]
+            val = r["nodes"] * ws * st / bt["sec"] / 1e9
             variants[v] = {
-                "workload": (f"64-instance 2D RB ensemble, N in {{129,257,513,1025}}, log10 Ra in [5,8], "
-                             f"Pr in {{0.71,7}}, {r['prec'].upper()} storage, {r['nodes']} nodes"),
-                "steps": st, "unit": "GLUPS",
-                "value": r["nodes"] * ws * st / bt["sec"] / 1e9,
-                "persistent_value": r["nodes"] * ws * st / r["persistent"]["sec"] / 1e9,
-                "persistent_launches": r["persistent"]["launches"],
-                "separate_launches_value": r["nodes"] * ws * st / sp["sec"] / 1e9,
-                "speedup_vs_separate": sp["sec"] / bt["sec"],
-                "batched_launches": bt["launches"], "separate_launches": sp["launches"],
-                "variant": bt["variant"], "diverged_instances": bt["diverged"],
+                "value": round(val, 3), "frac": round(val * bpl / peaks["hbm_gbs"], 4),
+                "persistent": round(r["nodes"] * ws * st / r["persistent"]["sec"] / 1e9, 3),
+                "separate": round(r["nodes"] * ws * st / sp["sec"] / 1e9, 3),
+                "speedup": round(sp["sec"] / bt["sec"], 3), "diverged": bt["diverged"],
             }
             continue
         st = args.steps if not v.endswith("fp64") else max(10, args.steps // 10)
         if v.startswith("3d"):
-            st = max(10, st // 2)
+            st = max(10, st // 2) if not v.endswith("fp64") else max(5, args.steps // 20)
         r = run_gpu(v, st, args.warmup if not v.endswith("fp64") else 3, ws, local, e2e=False)
         bpl = BYTES_PER_LU[(r["dim"], r["prec"])]
+        glups = r["nodes"] * ws * st / r["sec_max"] / 1e9
         gbs = bpl * r["nodes"] * st / r["sec"] / 1e9
-        variants[v] = {"workload": describe(v), "steps": st, "value": r["nodes"] * ws * st / r["sec_max"] / 1e9,
-                       "unit": "GLUPS", "ms_per_step": r["sec_max"] / st * 1e3,
-                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                    "frac": gbs / peaks["hbm_gbs"], "bytes_per_lu": bpl},
-                       "diverged": r["diverged"], "nusselt": r["nusselt"], "ekin_per_node": r["ekin_per_node"],
-                       "mass_drift": r["mass_drift"], "device_bytes": r["device_bytes"]}
+        rec = {"value": round(glups, 3), "ms": round(r["sec_max"] / st * 1e3, 4),
+               "frac": round(gbs / peaks["hbm_gbs"], 4)}
+        if r["prec"] == "fp64":
+            # FP64 roof: the measured FMA rate (FLOP/s, 2 per DFMA) and, for the
+            # kernel's uncontracted mix, the FP64 instruction rate (half of it)
+            ops = FP64_OPS_PER_LU[r["dim"]]
+            flop = ops["dadd"] + ops["dmul"] + 2 * ops["dfma"]
+            inst = ops["dadd"] + ops["dmul"] + ops["dfma"]
+            rate = r["nodes"] * st / r["sec"]
+            peak = fp64_peak()
+            rec["roofline"] = {"bound": "fp64", "achieved": round(flop * rate / 1e12, 4),
+                               "peak": round(peak / 1e12, 4), "unit": "TFLOP/s",
+                               "frac": round(flop * rate / peak, 4),
+                               "pipe_frac": round(inst * rate / (peak / 2), 4)}
+        if r["diverged"]:
+            rec["diverged"] = True
+        variants[v] = rec
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -578,6 +607,8 @@ def main():
         "mass_drift": r["mass_drift"],
         "diverged": r["diverged"],
         "variants": variants,
+        "variant_keys": "value GLUPS; ms per step; frac = algorithmic bytes / time / measured HBM copy peak; "
+                        "batch: persistent / separate = GLUPS of the persistent form / of 64 separate launches",
     }
     if "e2e" in r:
         e = r["e2e"]

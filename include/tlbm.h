@@ -245,8 +245,10 @@ TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bloc
  * blocks move each tile (one row segment of tile_width nodes) with TMA bulk
  * copies: one warp copies the tile's source row of every population into
  * shared memory (completing on mbarriers), 4 or 8 warps collide two nodes per
- * thread and write the results back in place, and the tile leaves with bulk
- * copies shared -> global; `stages` tiles are in flight per block.
+ * thread and store them straight to global memory; `stages` tiles are in
+ * flight per block.  Handles with FP16/BF16 storage and two-relaxation-time
+ * rates start on this kernel (tile_width 512; stages automatic in 2D, 2 in 3D)
+ * unless tlbm_set_variant was called.
  * tile_width: a multiple of 16 bytes' worth of elements, at most 512 (0 =
  * whole rows up to 512 nodes, else 512); stages: 2 .. 8 (0 = the most tiles in
  * flight per SM, blocks x stages, up to six, more blocks first).  FP32/FP16/BF16 storage with two-relaxation-time rates
@@ -423,6 +425,15 @@ TLBM_API int tlbm_upsample_bilinear(const float* in, int channels, int h, int w,
  * (other streams, handles or threads) race.  Runs on h's stream and
  * synchronises it. */
 TLBM_API int tlbm_reduce_noalloc(tlbm_t h, const void* state, double* out);
+
+/* Measured FP64 arithmetic roof of the current device (the paper has no
+ * counterpart; it is the roofline of the FP64 storage path, which the FP64
+ * pipes bind before HBM does on GB300): FLOP/s of independent FP64 fused
+ * multiply-adds (2 FLOP each) over every SM, best of a few launches of about
+ * 20 ms timed with CUDA events on `stream` (a cudaStream_t; NULL = legacy
+ * stream), which it synchronises.  Allocates nothing.  TLBM_ERR_ARG if
+ * flops_per_second is NULL, TLBM_ERR_CUDA on a CUDA error. */
+TLBM_API int tlbm_fp64_fma_rate(void* stream, double* flops_per_second);
 
 /* Text of the last error on this handle ("" if none); valid until the next call
  * on the handle.  A NULL handle returns the last error of a failed tlbm_create

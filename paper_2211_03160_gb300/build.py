@@ -35,6 +35,7 @@ UNITS = {
     "step_staged.cu": [],
     "batch.cu": [],
     "conv.cu": [],
+    "peak.cu": [],
 }
 
 

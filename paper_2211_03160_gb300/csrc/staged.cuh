@@ -80,13 +80,29 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
+// The same with a suspend-time hint: a thread whose phase has not completed is
+// parked until it completes or hint_ns have passed.  Without the hint a waiting
+// warp returned to the loop below, re-reading the clock, about 20 times per
+// tile (profile of the 3D FP16 staged kernel at 257^3).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return done != 0;
+}
 // Wait for the phase of `parity` to complete; false after `limit_ns` (0: false
 // unless it has completed when first tested).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
     if (limit_ns == 0) return mbar_test_wait(bar, parity);
-    if (mbar_try_wait(bar, parity)) return true;
+    constexpr uint32_t HINT_NS = 1000000;  // park for at most 1 ms per try
+    if (mbar_try_wait_hint(bar, parity, HINT_NS)) return true;
     const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait_hint(bar, parity, HINT_NS))
         if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
@@ -136,12 +152,17 @@ struct TileGeo {
     static constexpr int LW = TWMAX + 2 * A;
 };
 
-// Register caps: the 2D instance with 8 consumer warps fits in 72 registers
-// without spilling, which leaves room for three blocks per SM (27 warps); with
-// two stages each that measured 114.8 GLUPS at 8193^2 FP16 against 113.1 for
-// two blocks of 96 registers with three stages (GB300, same box).
+// Register caps.  An SM sub-partition holds 16384 registers, so a cap of R
+// registers leaves room for floor(16384 / (32 R)) warps on each of the four,
+// and a block of 1 + NC warps fits as often as those warps allow.  The 2D
+// instance with 8 consumer warps fits in 72 registers without spilling: three
+// blocks per SM (27 warps); with two stages each that measured 114.8 GLUPS at
+// 8193^2 FP16 against 113.1 for two blocks of 96 registers with three stages.
+// The 3D instance with 8 consumer warps spills 4 bytes at 96 registers, which
+// still fits two blocks per SM (at 112 only one: 4 warps per sub-partition):
+// 48.4 GLUPS at 385^3 FP16 against 40.0 (GB300, same box).
 template <int DIM, class S, int NC>
-__global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 112 : 168))
+__global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 96 : 168))
     step_staged_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p, const StagedInfo si) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
@@ -173,7 +194,13 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 112 : 168))
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         // producer: tile t = (row r, segment k), row r = (y, z); the tile's
-        // coordinates go to the stage header for the consumers
+        // coordinates go to the stage header for the consumers; lane j < Q
+        // copies population j (x-component ex of its velocity)
+        int ex = 0;
+        static_for<Q>([&](auto jj) {
+            constexpr int j = decltype(jj)::value;
+            if (lane == j) ex = j < QF ? LF::e(j < QF ? j : 0, 0) : LG::e(j < QF ? 0 : j - QF, 0);
+        });
         int i = 0;
         int s = 0, ph = 0;  // stage and the parity of its current use
         for (int t = blockIdx.x; t < si.tiles; t += G, ++i) {
@@ -186,16 +213,19 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 112 : 168))
             const unsigned z = r / (unsigned)L.ny;
             const int y = (int)(r - z * (unsigned)L.ny);
             const int tw = min(si.tw, L.nx - x0);
-            const int lo = x0 - A;
-            const int end = (x0 + tw + 1 + A - 1) / A * A;  // covers x0 + tw (the right neighbour)
-            const uint32_t bytes = (uint32_t)(end - lo) * (uint32_t)sizeof(S);
+            // population `lane` needs x0 - 1 only if e_x = +1 and x0 + tw only
+            // if e_x = -1; its copy starts and ends on 16-byte boundaries
+            const int lo = ex == 1 ? x0 - A : x0;
+            const int end = (x0 + tw + (ex == -1 ? 1 : 0) + A - 1) / A * A;
+            const uint32_t bytes = lane < Q ? (uint32_t)(end - lo) * (uint32_t)sizeof(S) : 0u;
+            const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
             if (lane == 0) {
                 head[s] = make_int4(x0, y, (int)z, tw);
-                mbar_arrive_expect_tx(&full[s], bytes * Q);
+                mbar_arrive_expect_tx(&full[s], total);
             }
             __syncwarp();
             if (lane < Q)
-                bulk_copy_g2s(stages + s * STAGE + lane * LW,
+                bulk_copy_g2s(stages + s * STAGE + lane * LW + (lo - (x0 - A)),
                               TLBM_DBG(p, (src + L.row(y, (int)z) + p.loff[lane] + lo), 0, (int)(bytes / sizeof(S))), bytes,
                               &full[s]);
             if (++s == NS) {

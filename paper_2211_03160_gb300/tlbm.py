@@ -84,6 +84,7 @@ _SIGS = {
     "tlbm_batch_set_rows": (C.c_int, [C.c_void_p, C.c_int]),
     "tlbm_batch_get_rows": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "tlbm_get_staged": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "tlbm_fp64_fma_rate": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "tlbm_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "tlbm_bounds_violations": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "tlbm_load": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -349,6 +350,15 @@ def tlbm_get_staged(h):
     tw, ns, nb = C.c_int(), C.c_int(), C.c_int()
     _check(h, lib().tlbm_get_staged(h, C.byref(tw), C.byref(ns), C.byref(nb)))
     return tw.value, ns.value, nb.value
+
+
+def tlbm_fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 FMA rate of the current device in FLOP/s."""
+    v = C.c_double()
+    rc = lib().tlbm_fp64_fma_rate(_cs(stream), C.byref(v))
+    if rc != 0:
+        raise TlbmError(rc, "tlbm_fp64_fma_rate failed")
+    return v.value
 
 
 def tlbm_set_wait_limit(h, seconds):
