@@ -244,13 +244,13 @@ TLBM_API int tlbm_set_variant(tlbm_t h, int vec, int form, int block_x, int bloc
 /* Use the shared-memory staged step kernel instead: a persistent grid whose
  * blocks move each tile (one row segment of tile_width nodes) with TMA bulk
  * copies: one warp copies the tile's source row of every population into
- * shared memory (completing on mbarriers), 4 or 8 warps collide two nodes per
- * thread and store them straight to global memory; `stages` tiles are in
- * flight per block.  Handles with FP16/BF16 storage and two-relaxation-time
- * rates start on this kernel (tile_width 512; stages automatic in 2D, 2 in 3D)
- * unless tlbm_set_variant was called.
- * tile_width: a multiple of 16 bytes' worth of elements, at most 512 (0 =
- * whole rows up to 512 nodes, else 512); stages: 2 .. 8 (0 = the most tiles in
+ * shared memory (completing on mbarriers), 4 or 8 warps (2D) or 4 or 7 warps
+ * (3D) collide two nodes per thread and store them straight to global memory;
+ * `stages` tiles are in flight per block.  Handles with FP16/BF16 storage and
+ * two-relaxation-time rates start on this kernel (whole rows; stages automatic
+ * in 2D, 2 in 3D) unless tlbm_set_variant was called.
+ * tile_width: a multiple of 16 bytes' worth of elements, at most 512 in 2D and
+ * 448 in 3D (0 = whole rows up to that width, else that width); stages: 2 .. 8 (0 = the most tiles in
  * flight per SM, blocks x stages, up to six, more blocks first).  FP32/FP16/BF16 storage with two-relaxation-time rates
  * only (TLBM_ERR_UNSUPPORTED otherwise).  A block that waits too long for its
  * copies gives up; the next synchronising call then returns TLBM_ERR_TIMEOUT.

@@ -715,11 +715,11 @@ extern "C" int tlbm_bind_memory(tlbm_t h, void* dev_ptr, size_t bytes) {
     // FP16/BF16 storage with two-relaxation-time rates defaults to the
     // shared-memory staged kernel: in 2D 512-node tiles with the stages chosen
     // as above (2 stages and three blocks per SM on GB300, the fastest there),
-    // in 3D whole rows with 2 stages and two blocks per SM (385^3: 48.4 GLUPS
-    // against 46.8 with 3 stages and 45.1 for the register kernel); the
+    // in 3D whole rows with 2 stages and two blocks per SM (385^3 FP16: 46.5
+    // GLUPS against 46.3 with 3 stages and 44.4 for the register kernel); the
     // register kernel stays if the device cannot host it
     if (!h->variant_chosen && !h->aa && (h->prec == TLBM_FP16_OFFSET || h->prec == TLBM_BF16_OFFSET) &&
-        h->kp.trt && set_staged(h, 512, h->dim == 3 ? 2 : 0) != TLBM_OK) {
+        h->kp.trt && set_staged(h, 0, h->dim == 3 ? 2 : 0) != TLBM_OK) {
         h->staged = 0;
         h->err[0] = 0;
     }
@@ -1151,7 +1151,18 @@ extern "C" int tlbm_load(tlbm_t h, const char* path) {
             char extra;
             if (fread(&extra, 1, 1, fp) != 0) rc = fail(h, TLBM_ERR_ARG, "%s is longer than its header says", path);
         }
-        if (rc == TLBM_OK) h->t = c.t;
+        if (rc == TLBM_OK) {
+            h->t = c.t;
+            // 16-bit storage: the step counter the time steps keep in word 0 of
+            // the current buffer (their stochastic rounding salt), as the
+            // uninterrupted run had it
+            if (h->elem == 2) {
+                const uint32_t t32 = (uint32_t)c.t;
+                cudaError_t e = cudaMemcpyAsync(h->buf[0], &t32, sizeof(t32), cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+                if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaMemcpyAsync (step counter)");
+            }
+        }
     }
     free(buf);
     fclose(fp);
@@ -1201,12 +1212,16 @@ static int set_staged(tlbm_t h, int tile_width, int stages) {
     if (!h->kp.trt) return fail(h, TLBM_ERR_UNSUPPORTED, "the staged kernel needs two-relaxation-time rates");
     const int A = 16 / (int)h->elem;
     const int nx_a = (h->nx + A - 1) / A * A;
-    // default: whole rows up to 512 nodes, else 512-node segments
-    int tw = tile_width > 0 ? tile_width : std::min(512, nx_a);
-    if (tw % A || tw < A || tw > 512)
-        return fail(h, TLBM_ERR_ARG, "tile_width must be a multiple of %d in [%d, 512]", A, A);
+    // default: whole rows up to the widest tile (512 nodes in 2D, 448 in 3D),
+    // else segments of that width
+    const int twmax = h->dim == 3 ? 448 : 512;
+    int tw = tile_width > 0 ? tile_width : std::min(twmax, nx_a);
+    if (tw % A || tw < A || tw > twmax)
+        return fail(h, TLBM_ERR_ARG, "tile_width must be a multiple of %d in [%d, %d]", A, A, twmax);
     if (tw > nx_a) tw = nx_a;
-    const int nc = tw > 256 ? 8 : 4;  // consumer warps: one pair of nodes per thread
+    // consumer warps (one pair of nodes per thread): 4 for tiles up to 256
+    // nodes, else 8 in 2D and 7 in 3D
+    const int nc = tw > 256 ? (h->dim == 3 ? 7 : 8) : 4;
     const int lw = 64 * nc + 2 * A;   // shared row length per population (elements)
     const size_t stage_bytes = (size_t)(h->qf + h->qg) * lw * h->elem;
     const void* fn = staged_function(h->dim, h->prec, nc);

@@ -190,6 +190,86 @@ __device__ __forceinline__ S from_c(C c) {
     else return S(c);
 }
 
+// ------------------------------------------------------------------ stochastic rounding
+//
+// FP16/BF16 storage rounds every value a time step stores stochastically: up
+// with probability equal to the dropped fraction of an ulp, so that a stored
+// value is exact in expectation.  Round to nearest drops every per-step change
+// below half an ulp; in a Rayleigh-Benard cell at 257^2 (about 4450 steps per
+// free-fall time, so populations change by ~2e-4 of their value per step) the
+// FP16 state then froze into a steady roll whose time-averaged Nusselt number
+// was 40 % below FP64, and convection never started from the noisy conductive
+// state.  The hardware conversion cvt.rs takes its random bits from a 32-bit
+// operand: for two packed values the upper value uses bits 31..16 (FP16: the 13
+// bits 28..16), the lower one bits 15..0 (FP16: 12..0); it rounds up when the
+// dropped bits plus those bits carry into the kept ones.  The bits of a value
+// are the top 16 bits of its FP32 pattern times 0x9E3779B1 (2^32 / golden
+// ratio): a deterministic function of the value alone, so every kernel variant
+// stores bitwise the same state, and a Weyl sequence in the value's low bits, so
+// that a value changing by a few units in its last place per step meets
+// equidistributed thresholds.  A value that does not change at all would meet
+// the same threshold every step (and round the same way, so that a nearly
+// frozen state stays frozen: a 129^2 cell at Ra = 2e4 never left its noisy
+// conductive start), so the key also adds a per-step salt, t times the same
+// constant, t being the step counter that the time steps keep in the first word
+// of each population buffer (step_count / advance_count below): the threshold
+// of a constant value then runs through a Weyl sequence over the steps.
+// Initial states and transfers (tlbm_init, tlbm_set_populations) round to
+// nearest.
+__device__ __forceinline__ uint32_t sr_key(float v, uint32_t salt) { return __float_as_uint(v) * 0x9E3779B1u + salt; }
+
+// (hi, lo) -> packed 16-bit pair, lo in the low half, stochastically rounded
+template <class S>
+__device__ __forceinline__ uint32_t cvt_rs2(float hi, float lo, uint32_t salt) {
+    const uint32_t r = __byte_perm(sr_key(lo, salt), sr_key(hi, salt), 0x7632);  // top16(hi) << 16 | top16(lo)
+    uint32_t d;
+    if constexpr (std::is_same<S, __half>::value)
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    else
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
+}
+
+// the value a time step stores: stochastically rounded for 16-bit storage (the
+// same threshold as it would get in the low half of a pair)
+template <class S, class C>
+__device__ __forceinline__ S from_c_step(C c, uint32_t salt) {
+    if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
+        const unsigned short b = (unsigned short)(cvt_rs2<S>(0.0f, (float)c, salt) & 0xffffu);
+        S v;
+        memcpy(&v, &b, 2);
+        return v;
+    } else {
+        return S(c);
+    }
+}
+
+template <class S>
+constexpr bool is16 = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+
+// The step counter of 16-bit storage: a 32-bit word at the start of each
+// population buffer (in the padding before slot (0, -1, -1), which no kernel
+// touches).  A two-buffer step reads word 0 of its source and writes the count
+// plus one into word 0 of its destination; the in-place halves alternate
+// between words 0 and 1 of their single buffer (AA_EVEN reads 0 and writes 1,
+// AA_ODD the reverse).  tlbm_init and tlbm_set_populations clear it with the
+// buffers, tlbm_load sets it to the restored step count.
+template <class S, bool CG = false>
+__device__ __forceinline__ uint32_t step_count(const S* buf, int word) {
+    if constexpr (!is16<S>) return 0u;
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(buf) + word;
+    if constexpr (CG) return __ldcg(w);
+    else return __ldg(w);
+}
+template <class S>
+__device__ __forceinline__ void advance_count(S* buf, int word, uint32_t t, bool writer) {
+    if constexpr (is16<S>) {
+        if (writer) reinterpret_cast<uint32_t*>(buf)[word] = t + 1u;
+    }
+}
+// the per-step salt of the stochastic rounding key
+__device__ __forceinline__ uint32_t step_salt(uint32_t t) { return t * 0x9E3779B9u; }
+
 // parameter accessors in the compute precision
 template <class C> struct PV;
 template <> struct PV<double> {
@@ -253,6 +333,17 @@ template <class S, class C>
 __device__ __forceinline__ S enc_g(C g, C scale) {
     if constexpr (Storage<S>::offset) return from_c<S>(g * scale);
     else return from_c<S>(g);
+}
+// the same as stored by a time step (stochastic rounding for 16-bit storage)
+template <class LF, class S, class C>
+__device__ __forceinline__ S enc_f_step(C d, int i, C scale, uint32_t salt) {
+    if constexpr (Storage<S>::offset) return from_c_step<S>(d * scale, salt);
+    else return from_c_step<S>(weight<LF, C>(i) + d, salt);
+}
+template <class S, class C>
+__device__ __forceinline__ S enc_g_step(C g, C scale, uint32_t salt) {
+    if constexpr (Storage<S>::offset) return from_c_step<S>(g * scale, salt);
+    else return from_c_step<S>(g, salt);
 }
 
 template <class C> struct ScaleOf;
@@ -821,7 +912,7 @@ constexpr int PULL = 0, AA_EVEN = 1, AA_ODD = 2;
 // for a wall, the image's own slot for a periodic face).
 template <class LS, bool THERMAL, int i, class S, class C, int MODE = PULL>
 __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams& p, int x, int y, int z, C val,
-                                            C scale) {
+                                            C scale, uint32_t salt) {
     constexpr int ex = LS::e(i, 0), ey = LS::e(i, 1), ez = LS::e(i, 2);
     if constexpr (ex == 0 && ey == 0 && ez == 0) return;
     const Layout& L = p.L;
@@ -850,8 +941,8 @@ __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams&
         // where the next AA_EVEN half reads it
         constexpr int plane = MODE == AA_EVEN ? i : o;
         const long long s = MODE == AA_ODD ? L.slot(x, y, z) : L.slot(dx, dy, dz);
-        if constexpr (THERMAL) *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_g<S, C>(out, scale);
-        else *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_f<LS, S, C>(out, plane, scale);
+        if constexpr (THERMAL) *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_g_step<S, C>(out, scale, salt);
+        else *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_f_step<LS, S, C>(out, plane, scale, salt);
     } else {
         // periodic: the value reaches the image node w = wrap(x + e_i) as f_i;
         // written by PULL: slot (w - e_i) of plane i; by AA_EVEN: slot (w - e_i)
@@ -862,8 +953,8 @@ __device__ __forceinline__ void ghost_write(S* __restrict__ base, const KParams&
         const int wz = oz ? (dz < 0 ? dz + L.nz : dz - L.nz) : dz;
         constexpr int plane = MODE == AA_EVEN ? o : i;
         const long long s = MODE == AA_ODD ? L.slot(wx, wy, wz) : L.slot(wx - ex, wy - ey, wz - ez);
-        if constexpr (THERMAL) *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_g<S, C>(val, scale);
-        else *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_f<LS, S, C>(val, plane, scale);
+        if constexpr (THERMAL) *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_g_step<S, C>(val, scale, salt);
+        else *TLBM_DBG(p, (base + ((long long)plane * L.plane + s)), 0, 1) = enc_f_step<LS, S, C>(val, plane, scale, salt);
     }
 }
 
@@ -882,14 +973,34 @@ __device__ __forceinline__ C raw_to_g_k(C raw, C inv_scale) {
     else return raw;
 }
 template <class LF, class S, class C, bool KS>
-__device__ __forceinline__ S enc_f_k(C d, int i, C scale) {
-    if constexpr (Storage<S>::offset) return from_c<S>(KS ? d : d * scale);
-    else return from_c<S>(weight<LF, C>(i) + d);
+__device__ __forceinline__ S enc_f_k(C d, int i, C scale, uint32_t salt) {
+    if constexpr (Storage<S>::offset) return from_c_step<S>(KS ? d : d * scale, salt);
+    else return from_c_step<S>(weight<LF, C>(i) + d, salt);
 }
 template <class S, class C, bool KS>
-__device__ __forceinline__ S enc_g_k(C g, C scale) {
-    if constexpr (Storage<S>::offset) return from_c<S>(KS ? g : g * scale);
-    else return from_c<S>(g);
+__device__ __forceinline__ S enc_g_k(C g, C scale, uint32_t salt) {
+    if constexpr (Storage<S>::offset) return from_c_step<S>(KS ? g : g * scale, salt);
+    else return from_c_step<S>(g, salt);
+}
+// The VEC values a thread stores for one population, encoded as enc_f_k /
+// enc_g_k would (flow: i >= 0 is its index; thermal: i < 0); 16-bit storage
+// converts them two at a time (one cvt.rs per pair, bitwise the scalar result).
+template <class LF, class S, class C, bool KS, int VEC>
+__device__ __forceinline__ void enc_vec(const C (&v)[VEC], int i, C scale, uint32_t salt, S (&out)[VEC]) {
+    constexpr bool h16 = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+    if constexpr (h16 && VEC % 2 == 0) {
+        static_assert(Storage<S>::offset, "16-bit storage is offset storage");
+#pragma unroll
+        for (int k = 0; k < VEC; k += 2) {
+            const float a = (float)(KS ? v[k] : v[k] * scale), b = (float)(KS ? v[k + 1] : v[k + 1] * scale);
+            const uint32_t d = cvt_rs2<S>(b, a, salt);
+            memcpy(&out[k], &d, 4);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k)
+            out[k] = i >= 0 ? enc_f_k<LF, S, C, KS>(v[k], i, scale, salt) : enc_g_k<S, C, KS>(v[k], scale, salt);
+    }
 }
 
 template <class LF, class S, class C>
@@ -932,7 +1043,7 @@ __device__ __forceinline__ void pull_node_vec(const S* __restrict__ own, const K
 // would otherwise crowd the instruction cache of the hot path.
 template <int DIM, class S, int VEC, class C, int MODE = PULL>
 __device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, int x0, int y, int z,
-                                         const C* __restrict__ post) {
+                                         const C* __restrict__ post, uint32_t salt) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
     constexpr int QF = LF::Q, QG = LG::Q;
@@ -943,11 +1054,11 @@ __device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, 
         if (x >= p.L.nx) break;
         static_for<QF>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            ghost_write<LF, false, i, S, C, MODE>(dst, p, x, y, z, post[i * VEC + k], scale);
+            ghost_write<LF, false, i, S, C, MODE>(dst, p, x, y, z, post[i * VEC + k], scale, salt);
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            ghost_write<LG, true, i, S, C, MODE>(gdst, p, x, y, z, post[(QF + i) * VEC + k], scale);
+            ghost_write<LG, true, i, S, C, MODE>(gdst, p, x, y, z, post[(QF + i) * VEC + k], scale, salt);
         });
     }
 }
@@ -957,7 +1068,7 @@ __device__ __noinline__ void edge_writes(S* __restrict__ dst, const KParams& p, 
 // periodic: those, and only those, leave the cell, through that face.
 template <class LS, bool THERMAL, int SIDE, class S, int VEC, class C, bool KS, int MODE = PULL>
 __device__ __forceinline__ void x_face(S* __restrict__ base, const KParams& p, int x, int y, int z, int k,
-                                       const C (&v)[LS::Q][VEC]) {
+                                       const C (&v)[LS::Q][VEC], uint32_t salt) {
     const C scale = ScaleOf<C>::s(p);
     const C un = KS ? ScaleOf<C>::inv(p) : C(1);  // the wall rules take unscaled values
     static_for<LS::Q>([&](auto ii) {
@@ -967,7 +1078,7 @@ __device__ __forceinline__ void x_face(S* __restrict__ base, const KParams& p, i
 #pragma unroll
             for (int kk = 1; kk < VEC; ++kk)
                 if (k == kk) val = v[i][kk];
-            ghost_write<LS, THERMAL, i, S, C, MODE>(base, p, x, y, z, KS ? val * un : val, scale);
+            ghost_write<LS, THERMAL, i, S, C, MODE>(base, p, x, y, z, KS ? val * un : val, scale, salt);
         }
     });
 }
@@ -978,7 +1089,8 @@ __device__ __forceinline__ void x_face(S* __restrict__ base, const KParams& p, i
 // general out-of-line path.
 template <int DIM, class S, int VEC, class C, bool KS, int MODE = PULL>
 __device__ __forceinline__ void wall_writes(S* __restrict__ dst, const KParams& p, int x0, int y, int z,
-                                            const C (&f)[Lat<DIM>::F::Q][VEC], const C (&g)[Lat<DIM>::G::Q][VEC]) {
+                                            const C (&f)[Lat<DIM>::F::Q][VEC], const C (&g)[Lat<DIM>::G::Q][VEC],
+                                            uint32_t salt) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
     constexpr int QF = LF::Q, QG = LG::Q;
@@ -995,18 +1107,18 @@ __device__ __forceinline__ void wall_writes(S* __restrict__ dst, const KParams& 
 #pragma unroll
             for (int i = 0; i < QG; ++i) post[(QF + i) * VEC + k] = KS ? g[i][k] * un : g[i][k];
         }
-        edge_writes<DIM, S, VEC, C, MODE>(dst, p, x0, y, z, post);
+        edge_writes<DIM, S, VEC, C, MODE>(dst, p, x0, y, z, post, salt);
         return;
     }
     S* __restrict__ gdst = dst + (long long)QF * L.plane;
     if (xlo) {
-        x_face<LF, false, -1, S, VEC, C, KS, MODE>(dst, p, 0, y, z, 0, f);
-        x_face<LG, true, -1, S, VEC, C, KS, MODE>(gdst, p, 0, y, z, 0, g);
+        x_face<LF, false, -1, S, VEC, C, KS, MODE>(dst, p, 0, y, z, 0, f, salt);
+        x_face<LG, true, -1, S, VEC, C, KS, MODE>(gdst, p, 0, y, z, 0, g, salt);
     }
     if (xhi) {
         const int k = L.nx - 1 - x0;
-        x_face<LF, false, 1, S, VEC, C, KS, MODE>(dst, p, L.nx - 1, y, z, k, f);
-        x_face<LG, true, 1, S, VEC, C, KS, MODE>(gdst, p, L.nx - 1, y, z, k, g);
+        x_face<LF, false, 1, S, VEC, C, KS, MODE>(dst, p, L.nx - 1, y, z, k, f, salt);
+        x_face<LG, true, 1, S, VEC, C, KS, MODE>(gdst, p, L.nx - 1, y, z, k, g, salt);
     }
 }
 
@@ -1031,6 +1143,9 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
     const C scale = ScaleOf<C>::s(p);
     const long long row = L.row(y, z);
     constexpr bool KS = TRT && Storage<S>::offset;  // TRT works on the stored, scaled values
+    const uint32_t tcount = step_count<S, CG>(src, 0);
+    const uint32_t salt = step_salt(tcount);
+    advance_count<S>(dst, 0, tcount, bx == 0 && by == 0 && bz == 0 && threadIdx.x == 0 && threadIdx.y == 0);
 
     C f[QF][VEC], g[QG][VEC];
     pull_node_vec<DIM, S, VEC, C, KS, CG>(src + row + x0ld, p, lane, f, g);
@@ -1043,15 +1158,13 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
         static_for<QF>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+            enc_vec<LF, S, C, KS, VEC>(f[i], i, scale, salt, v);
             st_vec<S, VEC>(TLBM_DBG(p, (own + p.soff[i]), 0, VEC), v);
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
+            enc_vec<LF, S, C, KS, VEC>(g[i], -1, scale, salt, v);
             st_vec<S, VEC>(TLBM_DBG(p, (own + p.soff[QF + i]), 0, VEC), v);
         });
     } else {
@@ -1060,18 +1173,18 @@ __device__ __forceinline__ void step_block(const S* __restrict__ src, S* __restr
             if (x0 + k < L.nx) {
                 static_for<QF>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    *TLBM_DBG(p, (own + (p.soff[i] + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                    *TLBM_DBG(p, (own + (p.soff[i] + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale, salt);
                 });
                 static_for<QG>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    *TLBM_DBG(p, (own + (p.soff[QF + i] + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale);
+                    *TLBM_DBG(p, (own + (p.soff[QF + i] + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale, salt);
                 });
             }
         }
     }
 
     // wall and periodic rules for values that leave the cell
-    wall_writes<DIM, S, VEC, C, KS>(dst, p, x0, y, z, f, g);
+    wall_writes<DIM, S, VEC, C, KS>(dst, p, x0, y, z, f, g, salt);
 }
 
 // ------------------------------------------------------------------ in-place (AA) streaming
@@ -1150,6 +1263,11 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
     const C inv_scale = ScaleOf<C>::inv(p);
     const long long row = L.row(y, z);
     constexpr bool KS = TRT && Storage<S>::offset;
+    // the step counter alternates between words 0 and 1 of the single buffer
+    const uint32_t tcount = step_count<S>(buf, MODE == AA_ODD ? 1 : 0);
+    const uint32_t salt = step_salt(tcount);
+    advance_count<S>(buf, MODE == AA_ODD ? 0 : 1, tcount,
+                     bx == 0 && by == 0 && bz == 0 && threadIdx.x == 0 && threadIdx.y == 0);
 
     C f[QF][VEC], g[QG][VEC];
     const S* own_ld = buf + row + x0ld;
@@ -1184,15 +1302,13 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
             static_for<QF>([&](auto ii) {
                 constexpr int i = decltype(ii)::value;
                 S v[VEC];
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                enc_vec<LF, S, C, KS, VEC>(f[i], i, scale, salt, v);
                 st_vec<S, VEC>(TLBM_DBG(p, (own + off_shift<LF::opp(i)>(p)), 0, VEC), v);
             });
             static_for<QG>([&](auto ii) {
                 constexpr int i = decltype(ii)::value;
                 S v[VEC];
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
+                enc_vec<LF, S, C, KS, VEC>(g[i], -1, scale, salt, v);
                 st_vec<S, VEC>(TLBM_DBG(p, (own + off_shift<QF + LG::opp(i)>(p)), 0, VEC), v);
             });
         } else {
@@ -1201,11 +1317,11 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
                 if (x0 + k < L.nx) {
                     static_for<QF>([&](auto ii) {
                         constexpr int i = decltype(ii)::value;
-                        *TLBM_DBG(p, (own + (off_shift<LF::opp(i)>(p) + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                        *TLBM_DBG(p, (own + (off_shift<LF::opp(i)>(p) + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale, salt);
                     });
                     static_for<QG>([&](auto ii) {
                         constexpr int i = decltype(ii)::value;
-                        *TLBM_DBG(p, (own + (off_shift<QF + LG::opp(i)>(p) + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale);
+                        *TLBM_DBG(p, (own + (off_shift<QF + LG::opp(i)>(p) + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale, salt);
                     });
                 }
             }
@@ -1221,17 +1337,17 @@ __device__ __forceinline__ void step_block_aa(S* buf, const KParams& p, int bx, 
         static_for<QF>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             push_row<S, VEC, LF::e(i, 0), C>(TLBM_AIM((own + off_shift<i, LF::e(i, 1), LF::e(i, 2)>(p))), lane, x0, L.nx, f[i],
-                                             [&](C d) { return enc_f_k<LF, S, C, KS>(d, i, scale); });
+                                             [&](C d) { return enc_f_k<LF, S, C, KS>(d, i, scale, salt); });
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             push_row<S, VEC, LG::e(i, 0), C>(TLBM_AIM((own + off_shift<QF + i, LG::e(i, 1), LG::e(i, 2)>(p))), lane, x0, L.nx, g[i],
-                                             [&](C d) { return enc_g_k<S, C, KS>(d, scale); });
+                                             [&](C d) { return enc_g_k<S, C, KS>(d, scale, salt); });
         });
 #undef TLBM_AIM
         if (x0 >= L.nx) return;
     }
-    wall_writes<DIM, S, VEC, C, KS, MODE>(buf, p, x0, y, z, f, g);
+    wall_writes<DIM, S, VEC, C, KS, MODE>(buf, p, x0, y, z, f, g, salt);
 }
 
 template <int DIM, class S, int VEC, bool TRT, int MODE>
@@ -1317,7 +1433,7 @@ __device__ __forceinline__ void decode_row(const RawRow<DIM, S, VEC>& r, const K
 template <int DIM, class S, int VEC, bool TRT, class C, bool KS>
 __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p, int x0, int y, int z,
                                            long long row, C (&f)[Lat<DIM>::F::Q][VEC],
-                                           C (&g)[Lat<DIM>::G::Q][VEC]) {
+                                           C (&g)[Lat<DIM>::G::Q][VEC], uint32_t salt) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
     constexpr int QF = LF::Q, QG = LG::Q;
@@ -1330,15 +1446,13 @@ __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p
         static_for<QF>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+            enc_vec<LF, S, C, KS, VEC>(f[i], i, scale, salt, v);
             st_vec<S, VEC>(TLBM_DBG(p, (own + p.soff[i]), 0, VEC), v);
         });
         static_for<QG>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             S v[VEC];
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = enc_g_k<S, C, KS>(g[i][k], scale);
+            enc_vec<LF, S, C, KS, VEC>(g[i], -1, scale, salt, v);
             st_vec<S, VEC>(TLBM_DBG(p, (own + p.soff[QF + i]), 0, VEC), v);
         });
     } else {
@@ -1347,16 +1461,16 @@ __device__ __forceinline__ void finish_row(S* __restrict__ dst, const KParams& p
             if (x0 + k < L.nx) {
                 static_for<QF>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    *TLBM_DBG(p, (own + (p.soff[i] + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale);
+                    *TLBM_DBG(p, (own + (p.soff[i] + k)), 0, 1) = enc_f_k<LF, S, C, KS>(f[i][k], i, scale, salt);
                 });
                 static_for<QG>([&](auto ii) {
                     constexpr int i = decltype(ii)::value;
-                    *TLBM_DBG(p, (own + (p.soff[QF + i] + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale);
+                    *TLBM_DBG(p, (own + (p.soff[QF + i] + k)), 0, 1) = enc_g_k<S, C, KS>(g[i][k], scale, salt);
                 });
             }
         }
     }
-    wall_writes<DIM, S, VEC, C, KS>(dst, p, x0, y, z, f, g);
+    wall_writes<DIM, S, VEC, C, KS>(dst, p, x0, y, z, f, g, salt);
 }
 
 // ROWS consecutive rows per thread, software-pipelined: the loads of the next
@@ -1378,6 +1492,9 @@ __device__ __forceinline__ void step_rows_block(const S* __restrict__ src, S* __
     if (x0 - lane * VEC >= L.nx) return;  // the whole warp lies past the row end
     const int x0ld = min(x0, p.xmax_load);
     const long long row0 = L.row(y0, z);
+    const uint32_t tcount = step_count<S>(src, 0);
+    const uint32_t salt = step_salt(tcount);
+    advance_count<S>(dst, 0, tcount, bx == 0 && by == 0 && bz == 0 && threadIdx.x == 0 && threadIdx.y == 0);
     RawRow<DIM, S, VEC> A, B;
     fetch_row<DIM, S, VEC>(src + row0 + x0ld, p, lane, A);
 #pragma unroll
@@ -1388,14 +1505,14 @@ __device__ __forceinline__ void step_rows_block(const S* __restrict__ src, S* __
         {
             C f[QF][VEC], g[QG][VEC];
             decode_row<DIM, S, VEC, C, KS>(A, p, lane, f, g);
-            finish_row<DIM, S, VEC, TRT, C, KS>(dst, p, x0, ya, z, rowa, f, g);
+            finish_row<DIM, S, VEC, TRT, C, KS>(dst, p, x0, ya, z, rowa, f, g, salt);
         }
         if (r + 1 >= ROWS || yb >= L.ny) break;
         if (r + 2 < ROWS && yb + 1 < L.ny) fetch_row<DIM, S, VEC>(src + rowa + 2 * L.P + x0ld, p, lane, A);
         {
             C f[QF][VEC], g[QG][VEC];
             decode_row<DIM, S, VEC, C, KS>(B, p, lane, f, g);
-            finish_row<DIM, S, VEC, TRT, C, KS>(dst, p, x0, yb, z, rowa + L.P, f, g);
+            finish_row<DIM, S, VEC, TRT, C, KS>(dst, p, x0, yb, z, rowa + L.P, f, g, salt);
         }
         if (yb + 1 >= L.ny) break;
     }

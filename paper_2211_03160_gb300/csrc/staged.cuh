@@ -130,17 +130,29 @@ template <class S> struct Pair;
 template <> struct Pair<float> {
     using T = float2;
     __device__ static float2 unpack(T v) { return v; }
-    __device__ static T pack(float a, float b) { return make_float2(a, b); }
+    __device__ static T pack(float a, float b, uint32_t) { return make_float2(a, b); }
 };
+// pack(a, b): a at the lower address; 16-bit storage rounds stochastically
+// (the time-step rounding of kernels.cuh, bitwise the scalar stores' result)
 template <> struct Pair<__half> {
     using T = __half2;
     __device__ static float2 unpack(T v) { return __half22float2(v); }
-    __device__ static T pack(float a, float b) { return __floats2half2_rn(a, b); }
+    __device__ static T pack(float a, float b, uint32_t salt) {
+        const uint32_t d = cvt_rs2<__half>(b, a, salt);
+        T v;
+        memcpy(&v, &d, 4);
+        return v;
+    }
 };
 template <> struct Pair<__nv_bfloat16> {
     using T = __nv_bfloat162;
     __device__ static float2 unpack(T v) { return __bfloat1622float2(v); }
-    __device__ static T pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    __device__ static T pack(float a, float b, uint32_t salt) {
+        const uint32_t d = cvt_rs2<__nv_bfloat16>(b, a, salt);
+        T v;
+        memcpy(&v, &d, 4);
+        return v;
+    }
 };
 
 // Stage geometry of a kernel with NC consumer warps: tiles of up to 64 NC nodes,
@@ -155,14 +167,17 @@ struct TileGeo {
 // Register caps.  An SM sub-partition holds 16384 registers, so a cap of R
 // registers leaves room for floor(16384 / (32 R)) warps on each of the four,
 // and a block of 1 + NC warps fits as often as those warps allow.  The 2D
-// instance with 8 consumer warps fits in 72 registers without spilling: three
-// blocks per SM (27 warps); with two stages each that measured 114.8 GLUPS at
-// 8193^2 FP16 against 113.1 for two blocks of 96 registers with three stages.
-// The 3D instance with 8 consumer warps spills 4 bytes at 96 registers, which
-// still fits two blocks per SM (at 112 only one: 4 warps per sub-partition):
-// 48.4 GLUPS at 385^3 FP16 against 40.0 (GB300, same box).
+// instance with 8 consumer warps fits in 72 registers: three blocks per SM (27
+// warps); with two stages each that measured 114.8 GLUPS at 8193^2 FP16 (round
+// to nearest) against 113.1 for two blocks of 96 registers with three stages,
+// and with stochastic rounding (20 bytes spilled) 102.9 against 93.7 for 7
+// consumer warps at 80.  The 3D instance runs 7 consumer warps (tiles up to 448
+// nodes, one 385-node row) at 128 registers: two 8-warp blocks per SM without
+// spilling, 46.5 GLUPS at 385^3 FP16 against 37.2 for 8 consumer warps held to
+// 96 (156 bytes spilled; 48.1 there before stochastic rounding).  GB300, same
+// box each.
 template <int DIM, class S, int NC>
-__global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 96 : 168))
+__global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 7 ? 128 : 168))
     step_staged_kernel(const S* __restrict__ src, S* __restrict__ dst, const KParams p, const StagedInfo si) {
     using LF = typename Lat<DIM>::F;
     using LG = typename Lat<DIM>::G;
@@ -192,6 +207,9 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 96 : 168))
 
     const int G = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // step counter of 16-bit storage (stochastic rounding salt)
+    const uint32_t tcount = step_count<S>(src, 0);
+    advance_count<S>(dst, 0, tcount, blockIdx.x == 0 && threadIdx.x == 0);
     if (warp == 0) {
         // producer: tile t = (row r, segment k), row r = (y, z); the tile's
         // coordinates go to the stage header for the consumers; lane j < Q
@@ -245,6 +263,7 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 96 : 168))
     // consumers: thread c updates nodes x0 + 2c and x0 + 2c + 1 of each tile
     const int c = threadIdx.x - 32;
     const int xr = 2 * c;
+    const uint32_t salt = step_salt(tcount);
     const float scale = ScaleOf<float>::s(p);
     const float inv_scale = ScaleOf<float>::inv(p);
     int s = 0, ph = 0;
@@ -293,21 +312,21 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 96 : 168))
             static_for<QF>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
                 *reinterpret_cast<S2*>(TLBM_DBG(p, (own + p.soff[q]), 0, 2)) =
-                    P2::pack(enc_val_f<LF, S, KS>(fd[q].x, q, scale), enc_val_f<LF, S, KS>(fd[q].y, q, scale));
+                    P2::pack(enc_val_f<LF, S, KS>(fd[q].x, q, scale), enc_val_f<LF, S, KS>(fd[q].y, q, scale), salt);
             });
             static_for<QG>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
                 *reinterpret_cast<S2*>(TLBM_DBG(p, (own + p.soff[QF + q]), 0, 2)) =
-                    P2::pack(enc_val_g<S, KS>(gd[q].x, scale), enc_val_g<S, KS>(gd[q].y, scale));
+                    P2::pack(enc_val_g<S, KS>(gd[q].x, scale), enc_val_g<S, KS>(gd[q].y, scale), salt);
             });
         } else {
             static_for<QF>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
-                *TLBM_DBG(p, (own + p.soff[q]), 0, 1) = enc_f_k<LF, S, float, KS>(fd[q].x, q, scale);
+                *TLBM_DBG(p, (own + p.soff[q]), 0, 1) = enc_f_k<LF, S, float, KS>(fd[q].x, q, scale, salt);
             });
             static_for<QG>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
-                *TLBM_DBG(p, (own + p.soff[QF + q]), 0, 1) = enc_g_k<S, float, KS>(gd[q].x, scale);
+                *TLBM_DBG(p, (own + p.soff[QF + q]), 0, 1) = enc_g_k<S, float, KS>(gd[q].x, scale, salt);
             });
         }
         float f2[QF][2], g2[QG][2];
@@ -315,7 +334,7 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 8 ? 96 : 168))
         for (int q = 0; q < QF; ++q) { f2[q][0] = fd[q].x; f2[q][1] = fd[q].y; }
 #pragma unroll
         for (int q = 0; q < QG; ++q) { g2[q][0] = gd[q].x; g2[q][1] = gd[q].y; }
-        wall_writes<DIM, S, 2, float, KS>(dst, p, x0 + xr, y, z, f2, g2);
+        wall_writes<DIM, S, 2, float, KS>(dst, p, x0 + xr, y, z, f2, g2, salt);
     }
 }
 

@@ -1,5 +1,6 @@
 // Shared-memory staged (TMA bulk copy) variants of the fused step, TRT form,
-// with 4 or 8 consumer warps (tiles of up to 256 or 512 nodes).
+// with 4 or 8 consumer warps in 2D (tiles of up to 256 or 512 nodes) and 4 or 7
+// in 3D (256 or 448).
 #include "dispatch.h"
 #include "staged.cuh"
 
@@ -23,11 +24,11 @@ static cudaError_t staged_dispatch(int dim, int prec, int nc, bool launch, const
     TLBM_STAGED_CASE(2, __nv_bfloat16, 3, 4)
     TLBM_STAGED_CASE(2, __nv_bfloat16, 3, 8)
     TLBM_STAGED_CASE(3, float, 1, 4)
-    TLBM_STAGED_CASE(3, float, 1, 8)
+    TLBM_STAGED_CASE(3, float, 1, 7)
     TLBM_STAGED_CASE(3, __half, 2, 4)
-    TLBM_STAGED_CASE(3, __half, 2, 8)
+    TLBM_STAGED_CASE(3, __half, 2, 7)
     TLBM_STAGED_CASE(3, __nv_bfloat16, 3, 4)
-    TLBM_STAGED_CASE(3, __nv_bfloat16, 3, 8)
+    TLBM_STAGED_CASE(3, __nv_bfloat16, 3, 7)
     if (!fn) return cudaErrorInvalidValue;
     return launch ? cudaGetLastError() : cudaSuccess;
 }

@@ -169,7 +169,7 @@ def test_variants_agree_bitwise(T):
                 g.step(20)
                 outs.append(g.get_populations())
                 g.close()
-        for tw, ns in ((0, 0), (16, 3), (64, 4), (256, 0), (512, 2)):
+        for tw, ns in ((0, 0), (16, 3), (64, 4), (256, 0), (512 if lattice == D2 else 448, 2)):
             g = T.Sim(*shape, lattice=lattice, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
             g.set_staged(tw, ns)
             g.init(11, 1e-3)
@@ -196,10 +196,12 @@ def test_init_matches_oracle(T, O, prec, lattice, shape):
 
 # ------------------------------------------------------------------ reduced precision vs FP64
 
-@pytest.mark.parametrize("prec,tol_T,tol_u", [(FP32, 2e-5, 1e-3), (FP16, 3e-2, 0.25), (BF16, 0.1, 1.0)])
+@pytest.mark.parametrize("prec,tol_T,tol_u", [(FP32, 2e-5, 3e-5), (FP16, 4e-3, 6e-3), (BF16, 3e-2, 5e-2)])
 def test_reduced_precision_fields_vs_oracle(T, O, prec, tol_T, tol_u):
     """129^2, Ra = 1e5, 400 steps: field error max|a - b| / max|b| (velocity
-    components scaled by the largest velocity component)."""
+    components scaled by the largest velocity component).  Measured: FP32 T
+    7.7e-6, u 1.2e-5; FP16 2.0e-3, 2.7e-3; BF16 1.5e-2, 2.5e-2 (16-bit storage
+    rounding stochastically); the bounds are about twice those."""
     g = T.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1, precision=prec)
     o = O.Sim(129, 129, lattice=D2, Ra=1e5, Pr=0.71, Ma=0.1)
     g.init(1, 1e-3)
@@ -367,9 +369,10 @@ def test_staged_at_bench_size(T):
 
 
 def test_staged_default_configuration(T):
-    """2D FP16/BF16 default to the staged kernel with 512-node tiles and the
-    stage count that keeps at most six tiles in flight per SM; tlbm_get_staged
-    reports it, and the register kernels report zeros."""
+    """FP16/BF16 default to the staged kernel: in 2D 512-node tiles and the
+    stage count that keeps at most six tiles in flight per SM, in 3D whole rows
+    (up to 448 nodes) with 2 stages; tlbm_get_staged reports it, and the
+    register kernels report zeros."""
     import torch
 
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -379,6 +382,10 @@ def test_staged_default_configuration(T):
         assert tw == 512 and 2 <= ns <= 8 and nb % sms == 0 and (nb // sms) * ns <= 6, (tw, ns, nb)
         g.set_variant(4, 2, 32, 1, 1)
         assert g.staged == (0, 0, 0)
+        g.close()
+        g = T.Sim(385, 33, 33, lattice=D3, Ra=1e6, Pr=0.71, Ma=0.1, precision=prec)
+        tw, ns, nb = g.staged
+        assert tw == 392 and ns == 2 and nb % sms == 0, (tw, ns, nb)
         g.close()
 
 
