@@ -37,9 +37,9 @@ struct BatchInst {
 // Called by all threads of a block together.  CG: the loads bypass L1 (the
 // persistent kernel reads what other blocks wrote in the previous step).  ROWS
 // > 1: the software-pipelined body (ROWS rows per thread; flattened form only).
-template <int DIM, class S, int VEC, bool TRT, bool CG = false, int ROWS = 1>
-__device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
-                                           int parity, long long b, KParams& sp, int& si) {
+// batch_stage: find the instance of tile b and stage its parameters in sp, si.
+__device__ __forceinline__ void batch_stage(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
+                                            long long b, KParams& sp, int& si) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nt = blockDim.x * blockDim.y;
     if (n <= 128) {
@@ -73,7 +73,13 @@ __device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, cons
         for (int w = tid; w < (int)(sizeof(KParams) / sizeof(long long)); w += nt) dst[w] = src[w];
     }
     __syncthreads();
-    const BatchInst in = inst[i];
+}
+
+// batch_run: step tile b of the staged instance si.
+template <int DIM, class S, int VEC, bool TRT, bool CG = false, int ROWS = 1>
+__device__ __forceinline__ void batch_run(const BatchInst* __restrict__ inst, int parity, long long b,
+                                          const KParams& sp, int si) {
+    const BatchInst in = inst[si];
     const long long local = b - in.block0;
     const int bx = (int)(local % in.gx);
     const long long r = local / in.gx;
@@ -87,12 +93,34 @@ __device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, cons
     }
 }
 
+template <int DIM, class S, int VEC, bool TRT, bool CG = false, int ROWS = 1>
+__device__ __forceinline__ void batch_tile(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
+                                           int parity, long long b, KParams& sp, int& si) {
+    batch_stage(kps, inst, n, b, sp, si);
+    batch_run<DIM, S, VEC, TRT, CG, ROWS>(inst, parity, b, sp, si);
+}
+
+// Flattened form: block k steps the tiles [k tpb, (k + 1) tpb) in order.  The
+// tiles of an instance are consecutive, so a block stages an instance's
+// parameters only when its run of tiles enters that instance (one tile per
+// block staged them for every tile, a lookup and a 1.2 KB copy in front of
+// every 1024 nodes).
 template <int DIM, class S, int VEC, bool TRT, int ROWS = 1>
 __global__ void batch_step_kernel(const KParams* __restrict__ kps, const BatchInst* __restrict__ inst, int n,
-                                  int parity) {
+                                  int parity, long long tiles, int tpb) {
     __shared__ KParams sp;
     __shared__ int si;
-    batch_tile<DIM, S, VEC, TRT, false, ROWS>(kps, inst, n, parity, blockIdx.x, sp, si);
+    const long long b0 = (long long)blockIdx.x * tpb;
+    const long long b1 = b0 + tpb < tiles ? b0 + tpb : tiles;
+    long long next = -1;  // first tile past the staged instance
+    for (long long b = b0; b < b1; ++b) {
+        if (b >= next) {
+            if (next >= 0) __syncthreads();  // every thread is done with sp
+            batch_stage(kps, inst, n, b, sp, si);
+            next = si + 1 < n ? inst[si + 1].block0 : tiles;
+        }
+        batch_run<DIM, S, VEC, TRT, false, ROWS>(inst, parity, b, sp, si);
+    }
 }
 
 // ------------------------------------------------------------------ persistent form
@@ -194,7 +222,8 @@ struct Persist {
                                                dim3((unsigned)grid), block, args, 0, s);            \
         }                                                                                           \
         if (launch)                                                                                 \
-            batch_step_kernel<DIM, S, VEC, TRT><<<grid, block, 0, s>>>(kps, inst, n, parity);       \
+            batch_step_kernel<DIM, S, VEC, TRT>                                                     \
+                <<<(grid + tpb - 1) / tpb, block, 0, s>>>(kps, inst, n, parity, grid, tpb);         \
         return launch ? cudaGetLastError() : cudaSuccess;                                           \
     }
 
@@ -203,13 +232,14 @@ struct Persist {
     if (dim == DIM && prec == PREC && vec == VEC && trt && rows == ROWS) {                           \
         if (pp) return cudaErrorInvalidValue;                                                         \
         if (launch)                                                                                   \
-            batch_step_kernel<DIM, S, VEC, true, ROWS><<<grid, block, 0, s>>>(kps, inst, n, parity);  \
+            batch_step_kernel<DIM, S, VEC, true, ROWS>                                                \
+                <<<(grid + tpb - 1) / tpb, block, 0, s>>>(kps, inst, n, parity, grid, tpb);           \
         return launch ? cudaGetLastError() : cudaSuccess;                                             \
     }
 
 cudaError_t batch_dispatch(bool launch, int dim, int prec, int vec, bool trt, const KParams* kps,
                            const BatchInst* inst, int n, int parity, long long grid, dim3 block, cudaStream_t s,
-                           const Persist* pp = nullptr, int rows = 1) {
+                           const Persist* pp = nullptr, int rows = 1, int tpb = 1) {
     TLBM_BATCH_ROWS_CASE(2, float, 1, 4, 2)
     TLBM_BATCH_ROWS_CASE(2, __half, 2, 4, 2)
     TLBM_BATCH_ROWS_CASE(2, __half, 2, 8, 2)
@@ -260,6 +290,7 @@ struct tlbm_batch_s {
     GridSync* d_sync;
     int vec, trt, bx, by;
     int rows;           // rows per thread of the flattened launch (1 or 2)
+    int tpb;            // tiles per block of the flattened launch
     int graph_steps;
     int persist_steps;  // > 0: persistent kernel, this many steps per launch
     unsigned long long wait_ns;  // grid-barrier wait limit of the persistent kernel
@@ -353,7 +384,7 @@ static int upload_tables(tlbm_batch_t b) {
 
 static cudaError_t launch_batch(tlbm_batch_t b, int parity, cudaStream_t s) {
     return batch_dispatch(true, b->dim, b->prec, b->vec, b->trt != 0, b->d_kp, b->d_inst, b->n, parity,
-                          b->total_blocks, dim3(b->bx, b->by, 1), s, nullptr, eff_rows(b));
+                          b->total_blocks, dim3(b->bx, b->by, 1), s, nullptr, eff_rows(b), b->tpb);
 }
 
 extern "C" int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* instances, int lattice,
@@ -372,6 +403,7 @@ extern "C" int tlbm_batch_create(tlbm_batch_t* out, int n, const tlbm_instance* 
     b->dim = lattice == TLBM_D3Q19_D3Q7 ? 3 : 2;
     b->graph_steps = 16;
     b->rows = 1;
+    b->tpb = 8;
     b->wait_ns = GRID_WAIT_NS;
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
@@ -610,7 +642,7 @@ extern "C" int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* 
 // Tuned launch shapes of this process, per (lattice, storage, collision form,
 // size class = floor(log2(total nodes))).
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int>, std::array<int, 4>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int>, std::array<int, 5>> g_tune_cache;
 
 static std::tuple<int, int, int, int> tune_key(tlbm_batch_t b) {
     long long nodes = 0;
@@ -636,6 +668,7 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
             b->bx = it->second[1];
             b->by = it->second[2];
             b->rows = it->second[3];
+            b->tpb = it->second[4];
             return upload_tables(b);
         }
     }
@@ -685,15 +718,41 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
         }
         if (rc != TLBM_OK) break;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->vec = bv;
     b->rows = brows;
     b->bx = bbx;
     b->by = bby;
+    // tiles per block of the flattened launch, for the chosen shape
+    int btpb = b->tpb;
+    if (rc == TLBM_OK && b->persist_steps <= 0 && (rc = upload_tables(b)) == TLBM_OK) {
+        best = 1e30f;
+        const int tpbs[] = {1, 2, 4, 8, 16, 32};
+        for (int tp : tpbs) {
+            b->tpb = tp;
+            cudaError_t e = launch_batch(b, b->parity, b->stream);  // warm
+            cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_batch(b, b->parity, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            b->launches += reps + 1;
+            if (ms < best) {
+                best = ms;
+                btpb = tp;
+            }
+        }
+        b->tpb = btpb;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     if (rc == TLBM_OK) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[tune_key(b)] = {bv, bbx, bby, brows};
+        g_tune_cache[tune_key(b)] = {bv, bbx, bby, brows, btpb};
     }
     int rc2 = upload_tables(b);
     return rc != TLBM_OK ? rc : rc2;

@@ -833,25 +833,28 @@ __device__ __forceinline__ void ld_vec(const S* __restrict__ p, S (&v)[VEC]) {
     }
 }
 
+// Stores of the populations, always to global memory (st.global): a buffer
+// pointer the batched kernels read from their instance table would otherwise
+// give generic stores.
 template <class S, int VEC>
 __device__ __forceinline__ void st_vec(S* __restrict__ p, const S (&v)[VEC]) {
     constexpr int B = VEC * (int)sizeof(S);
     if constexpr (B == 16) {
         uint4 t;
         memcpy(&t, v, 16);
-        *reinterpret_cast<uint4*>(p) = t;
+        __stwb(reinterpret_cast<uint4*>(p), t);
     } else if constexpr (B == 8) {
         uint2 t;
         memcpy(&t, v, 8);
-        *reinterpret_cast<uint2*>(p) = t;
+        __stwb(reinterpret_cast<uint2*>(p), t);
     } else if constexpr (B == 4) {
         unsigned int t;
         memcpy(&t, v, 4);
-        *reinterpret_cast<unsigned int*>(p) = t;
+        __stwb(reinterpret_cast<unsigned int*>(p), t);
     } else {
         unsigned short t;
         memcpy(&t, v, 2);
-        *reinterpret_cast<unsigned short*>(p) = t;
+        __stwb(reinterpret_cast<unsigned short*>(p), t);
     }
 }
 
@@ -866,7 +869,7 @@ __device__ __forceinline__ void pull_row(const S* __restrict__ q, int lane, C (&
     if constexpr (VEC == 1) {
         // one node per thread: a scalar load needs no alignment, fetch the
         // shifted element directly
-        out[0] = to_c<C>(CG ? ld_one<S, true>(q - EX) : q[-EX]);
+        out[0] = to_c<C>(ld_one<S, CG>(q - EX));
         return;
     }
     S v[VEC];
@@ -877,14 +880,14 @@ __device__ __forceinline__ void pull_row(const S* __restrict__ q, int lane, C (&
     } else if constexpr (EX == 1) {
         // node x pulls from x - 1
         C left = __shfl_up_sync(0xffffffffu, to_c<C>(v[VEC - 1]), 1);
-        if (lane == 0) left = to_c<C>(CG ? ld_one<S, true>(q - 1) : q[-1]);
+        if (lane == 0) left = to_c<C>(ld_one<S, CG>(q - 1));
         out[0] = left;
 #pragma unroll
         for (int k = 1; k < VEC; ++k) out[k] = to_c<C>(v[k - 1]);
     } else {
         // node x pulls from x + 1
         C right = __shfl_down_sync(0xffffffffu, to_c<C>(v[0]), 1);
-        if (lane == 31) right = to_c<C>(CG ? ld_one<S, true>(q + VEC) : q[VEC]);
+        if (lane == 31) right = to_c<C>(ld_one<S, CG>(q + VEC));
 #pragma unroll
         for (int k = 0; k < VEC - 1; ++k) out[k] = to_c<C>(v[k + 1]);
         out[VEC - 1] = right;
@@ -1381,13 +1384,13 @@ __device__ __forceinline__ void fetch_row(const S* __restrict__ own, const KPara
         constexpr int ex = j < LF::Q ? LF::e(j < LF::Q ? j : 0, 0) : LG::e(j < LF::Q ? 0 : j - LF::Q, 0);
         const S* __restrict__ q = TLBM_DBG(p, (own + p.loff[j]), 1, VEC + 2);
         if constexpr (VEC == 1) {
-            r.v[j][0] = q[-ex];
+            r.v[j][0] = ld_one<S, false>(q - ex);
         } else {
             ld_vec<S, VEC>(q, r.v[j]);
             if constexpr (ex == 1) {
-                if (lane == 0) r.h[j] = q[-1];
+                if (lane == 0) r.h[j] = ld_one<S, false>(q - 1);
             } else if constexpr (ex == -1) {
-                if (lane == 31) r.h[j] = q[VEC];
+                if (lane == 31) r.h[j] = ld_one<S, false>(q + VEC);
             }
         }
     });

@@ -66,8 +66,9 @@ def test_fp64_2d_config1_1000_2000_steps(T, O, kw):
 
 @pytest.mark.parametrize("kw", [{}, {"streaming": 1}], ids=["pull", "inplace"])
 def test_fp64_3d_parity(T, O, kw):
-    """D3Q19 + D3Q7 cube, 500 steps (walls on every face), both streaming schemes."""
-    n = 33
+    """D3Q19 + D3Q7 cube of 65^3 nodes, 500 steps (walls on every face), both
+    streaming schemes."""
+    n = 65
     g = T.Sim(n, n, n, lattice=D3, Ra=1e5, Pr=0.71, Ma=0.1, precision=FP64, **kw)
     o = O.Sim(n, n, n, lattice=D3, Ra=1e5, Pr=0.71, Ma=0.1)
     O.set_threads(8)
