@@ -376,6 +376,27 @@ def run_batch(prec: str, steps: int, warmup: int, ws: int, device_index: int) ->
     return out
 
 
+def warm_start_record():
+    """The learned warm start's measured gain on the 513^2 workload (16 held-out
+    draws, Ra 1e6-1e8): median ratio of steps to reach the conductive run's
+    steady Nusselt level, conductive / learned start, from the committed result
+    of `python -m paper_2211_03160_gb300.surrogate` (a run of several minutes,
+    not repeated here)."""
+    p = os.path.join(ROOT, "results", "warm_start_513.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        r = json.load(fh)
+    sm = r["summary"]
+    rec = {"unit": "x fewer steps to steady Nu", "source": "results/warm_start_513.json (not re-run by bench.py)"}
+    for k in ("coarse", "coords"):
+        if k in sm and sm[k]["reach"]["median_speedup"]:
+            rec[k] = round(sm[k]["reach"]["median_speedup"], 3)
+            rec[k + "_faster"] = f'{sm[k]["reach"]["faster"]}/{sm[k]["reach"]["compared"]}'
+    rec["value"] = rec.get("coarse", rec.get("coords"))
+    return rec
+
+
 _FP64_PEAK = None
 
 
@@ -565,6 +586,10 @@ def main():
         if r["diverged"]:
             rec["diverged"] = True
         variants[v] = rec
+
+    ws_rec = warm_start_record()
+    if ws_rec:
+        variants["warm_start_513"] = ws_rec
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -2,12 +2,18 @@
 
 A 4-layer 3x3 convolutional network (32 channels, ReLU, BF16 weights on the
 tensor cores with FP32 accumulation and FP32 Adam master weights) maps, at the
-65 x 65 coarse nodes of a 513 x 513 cell, the input channels
+65 x 65 coarse nodes of a 513 x 513 cell, five input channels to the
+time-averaged temperature and velocity (T, u/U, v/U) of the statistically
+steady flow.  Two input forms:
 
-    conductive temperature, x, y (unit square), (log10 Ra - 7) / 1.5, (Pr - 3.855) / 3.145
+    "coords": conductive temperature, x, y (unit square), (log10 Ra - 7) / 1.5,
+              (Pr - 3.855) / 3.145
+    "coarse": the time-averaged T, u/U, v/U of a cheap 65 x 65 run of the same
+              cell at the same (Ra, Pr) (the form the warm-start configuration
+              names), (log10 Ra - 7) / 1.5, (Pr - 3.855) / 3.145
 
-to the time-averaged temperature and velocity (T, u/U, v/U) of the statistically
-steady flow.  The prediction is upsampled vertex-aligned (coarse node (i, j) =
+the second paying for the coarse run, counted in fine-step equivalents (its
+steps times 65^2 / 513^2).  The prediction is upsampled vertex-aligned (coarse node (i, j) =
 fine node (8i, 8j)) and the solver starts from f = f_eq(1, u), g = g_eq(T, u)
 (tlbm_init_fields) instead of the conductive state.
 
@@ -52,6 +58,55 @@ def features(Ra: float, Pr: float, n: int = COARSE, fine: int = FINE) -> np.ndar
     x[3] = (math.log10(Ra) - 7.0) / 1.5
     x[4] = (Pr - 3.855) / 3.145
     return x
+
+
+def features_coarse(Ra: float, Pr: float, fields: np.ndarray) -> np.ndarray:
+    """Input channels of the "coarse" form: fields = (3, 65, 65) time-averaged
+    T, u/U, v/U of the 65 x 65 run."""
+    x = np.zeros((CIN,) + fields.shape[1:], dtype=np.float32)
+    x[0:3] = fields
+    x[3] = (math.log10(Ra) - 7.0) / 1.5
+    x[4] = (Pr - 3.855) / 3.145
+    return x
+
+
+def coarse_fields(draw_list, warm_tf: float = 30.0, avg_tf: float = 10.0, samples: int = 40,
+                  precision=tlbm.TLBM_FP32):
+    """Time-averaged (T, u/U, v/U) of a 65 x 65 run of each draw (same Ra, Pr,
+    seed), canonical roll sense; a run that diverged (the 65^2 cell is far too
+    coarse at the highest Ra) gives the conductive profile at rest.  Returns the
+    fields, the per-draw divergence flags and the steps of one run."""
+    import torch
+
+    n = COARSE
+    tf = free_fall_steps(n)
+    U = 0.1 / math.sqrt(3.0)
+    inst = [(n, n, 1, Ra, Pr, 0.1, seed) for Ra, Pr, seed in draw_list]
+    b = tlbm.Batch(inst, lattice=tlbm.TLBM_D2Q9_D2Q5, precision=precision)
+    b.init(1e-3)
+    b.step(int(warm_tf * tf))
+    every = max(1, int(avg_tf * tf / samples))
+    acc = torch.zeros((len(inst), 3, n, n), dtype=torch.float64, device="cuda")
+    T = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    ux = torch.empty_like(T)
+    uy = torch.empty_like(T)
+    for _ in range(samples):
+        b.step(every)
+        for k in range(len(inst)):
+            tlbm.tlbm_batch_macros(b.b, k, None, ux, uy, None, T, tlbm.TLBM_OUT_F32)
+            acc[k, 0] += T
+            acc[k, 1] += ux / U
+            acc[k, 2] += uy / U
+    status = b.status()
+    b.close()
+    out = (acc / samples).float().cpu().numpy()
+    yy = np.arange(n)[:, None]
+    for k in range(len(inst)):
+        if status[k] or not np.isfinite(out[k]).all():
+            out[k] = 0.0
+            out[k, 0] = 0.5 - (yy + 0.5) / n
+    steps = int(warm_tf * tf) + samples * every
+    return canonical_roll(out), status, steps
 
 
 def draws(n: int, seed: int, log_ra=(6.0, 8.0), prs=(0.71, 7.0)):
@@ -186,12 +241,14 @@ def factor(fine: int) -> int:
     return (fine - 1) // (COARSE - 1)
 
 
-def predict(net: ConvNet, Ra: float, Pr: float, fine: int = FINE):
-    """Coarse (3, 65, 65) FP32 prediction on the device: T, u/U, v/U."""
+def predict(net: ConvNet, Ra: float, Pr: float, fine: int = FINE, x: np.ndarray | None = None):
+    """Coarse (3, 65, 65) FP32 prediction on the device: T, u/U, v/U (x: the
+    input channels; default the "coords" form)."""
     import torch
 
     s = torch.cuda.current_stream()
-    x32 = torch.tensor(features(Ra, Pr, fine=fine)[None], dtype=torch.float32, device="cuda")
+    x = features(Ra, Pr, fine=fine) if x is None else x
+    x32 = torch.tensor(x[None], dtype=torch.float32, device="cuda")
     x16 = torch.empty(x32.shape, dtype=torch.bfloat16, device="cuda")
     tlbm.tlbm_to_bf16(x32, x32.numel(), x16, s)
     return net.forward(x16, 1, COARSE, COARSE)[0]
@@ -334,6 +391,73 @@ def evaluate(net: ConvNet, draw_list, run_tf: float, ref_tf: float, samples_per_
     return out, series
 
 
+def evaluate_starts(draw_list, starts: dict, run_tf: float, ref_tf: float, samples_per_tf: int = 16,
+                    precision=tlbm.TLBM_FP32, fine: int = FINE, extra_cost: dict | None = None):
+    """The conductive start and every learned start of `starts` (name -> list
+    of coarse (3, 65, 65) device predictions, one per draw) on the same draws,
+    in one batch.  extra_cost[name]: fine-step equivalents spent before the
+    start (a coarse run), added to its step counts.  Per draw: the reference Nu
+    (the conductive run's mean over its last ref_tf free-fall times) and, per
+    start, the steps to reach and to hold it (None if never)."""
+    import torch
+
+    tf = free_fall_steps(fine)
+    U = 0.1 / math.sqrt(3.0)
+    n = len(draw_list)
+    names = list(starts)
+    inst = [(fine, fine, 1, Ra, Pr, 0.1, seed) for Ra, Pr, seed in draw_list] * (1 + len(names))
+    b = tlbm.Batch(inst, lattice=tlbm.TLBM_D2Q9_D2Q5, precision=precision)
+    b.init(1e-3)
+    for g, name in enumerate(names):
+        for k in range(n):
+            warm_start(b.instance((g + 1) * n + k), starts[name][k], U, fine)
+    torch.cuda.synchronize()
+    dt = max(1, tf // samples_per_tf)
+    total = int(run_tf * samples_per_tf)
+    nus = np.zeros((len(inst), total))
+    for s_ in range(total):
+        b.step(dt)
+        nus[:, s_] = b.nusselt(allow_diverged=True)  # the status is recorded below
+    status = b.status()
+    b.close()
+    window = samples_per_tf // 2  # half a free-fall time
+    ref_samples = int(ref_tf * samples_per_tf)
+    extra_cost = extra_cost or {}
+    out = []
+    for k, (Ra, Pr, seed) in enumerate(draw_list):
+        ref = float(nus[k, -ref_samples:].mean())
+        e = {"Ra": Ra, "Pr": Pr, "Nu_ref": ref, "Nu_ref_rel_std": float(nus[k, -ref_samples:].std() / abs(ref)),
+             "steps_conductive": steps_to_reach(nus[k], dt, window, ref),
+             "held_conductive": steps_to_steady(nus[k], dt, window, ref),
+             "diverged": bool(status[k])}
+        for g, name in enumerate(names):
+            row = (g + 1) * n + k
+            cost = int(extra_cost.get(name, [0] * n)[k])
+            r, h = steps_to_reach(nus[row], dt, window, ref), steps_to_steady(nus[row], dt, window, ref)
+            e[f"steps_{name}"] = None if r is None else r + cost
+            e[f"held_{name}"] = None if h is None else h + cost
+            e[f"cost_{name}"] = cost
+            e["diverged"] = e["diverged"] or bool(status[row])
+        out.append(e)
+    return out, {"dt": dt, "samples_per_tf": samples_per_tf, "nu": np.round(nus, 5).tolist(), "starts": names}
+
+
+def summarize_starts(ev, names) -> dict:
+    """Per learned start: median step ratio conductive / learned for both
+    criteria, over the draws where both runs met it."""
+    res = {}
+    for name in names:
+        res[name] = {}
+        for key, a, b in (("reach", "steps_conductive", f"steps_{name}"),
+                          ("held", "held_conductive", f"held_{name}")):
+            both = [e for e in ev if e[a] and e[b] and not e["diverged"]]
+            res[name][key] = {"compared": len(both), "faster": sum(e[b] < e[a] for e in both),
+                              "median_speedup": float(np.median([e[a] / e[b] for e in both])) if both else None,
+                              "median_steps_conductive": float(np.median([e[a] for e in both])) if both else None,
+                              "median_steps_learned": float(np.median([e[b] for e in both])) if both else None}
+    return res
+
+
 def summarize(ev) -> dict:
     """Median step ratio conductive / warm for both criteria, over the draws
     where both runs met it."""
@@ -359,15 +483,19 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=3000)
     ap.add_argument("--run-tf", type=float, default=60.0)
     ap.add_argument("--ref-tf", type=float, default=20.0)
+    ap.add_argument("--coarse-warm-tf", type=float, default=30.0, help="65^2 run: free-fall times before averaging")
+    ap.add_argument("--coarse-avg-tf", type=float, default=10.0, help="65^2 run: free-fall times averaged")
     ap.add_argument("--fine", type=int, default=FINE, help="fine cell size, 64 k + 1")
     ap.add_argument("--log-ra", type=float, nargs=2, default=(6.0, 8.0), help="log10 Ra range of the draws")
-    ap.add_argument("--out", default="")
+    ap.add_argument("--input", default="both", choices=["coords", "coarse", "both"])
+    ap.add_argument("--out", default="", help="write the full result (per-draw steps and Nu series), JSON")
     ap.add_argument("--save-data", default="", help="write the generated training targets (.npz)")
     ap.add_argument("--load-data", default="", help="reuse training targets written by --save-data")
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
     t0 = time.time()
     tr = draws(args.train_draws, seed=1, log_ra=tuple(args.log_ra))
+    ev_draws = draws(args.eval_draws, seed=2, log_ra=tuple(args.log_ra))
     if args.load_data:
         z = np.load(args.load_data)
         Y, st = z["Y"], list(z["status"])
@@ -376,19 +504,40 @@ def main(argv=None):
     if args.save_data:
         np.savez(args.save_data, Y=Y, status=np.array(st))
     Y = canonical_roll(Y)
-    X = np.stack([features(Ra, Pr, fine=args.fine) for Ra, Pr, _ in tr])
     keep = [k for k in range(len(tr)) if not st[k] and np.isfinite(Y[k]).all()]
+    modes = ["coords", "coarse"] if args.input == "both" else [args.input]
     t1 = time.time()
-    net = ConvNet(seed=0)
-    hist = train(net, X[keep], Y[keep], iters=args.iters)
-    torch.cuda.synchronize()
-    t2 = time.time()
-    ev, series = evaluate(net, draws(args.eval_draws, seed=2, log_ra=tuple(args.log_ra)), args.run_tf, args.ref_tf,
-                          fine=args.fine)
-    t3 = time.time()
     res = {"fine": args.fine, "log_ra": list(args.log_ra), "train_draws": len(tr), "train_kept": len(keep),
-           "loss": hist, "summary": summarize(ev), "eval": ev, "series": series,
-           "seconds": {"data": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}
+           "eval_draws": len(ev_draws), "run_tf": args.run_tf, "ref_tf": args.ref_tf, "inputs": {}}
+    starts, costs = {}, {}
+    for mode in modes:
+        tm = time.time()
+        if mode == "coords":
+            X = np.stack([features(Ra, Pr, fine=args.fine) for Ra, Pr, _ in tr])
+            Xe = [features(Ra, Pr, fine=args.fine) for Ra, Pr, _ in ev_draws]
+            cost = [0] * len(ev_draws)
+            info = {}
+        else:
+            ftr, sttr, steps_c = coarse_fields(tr, args.coarse_warm_tf, args.coarse_avg_tf)
+            fev, stev, _ = coarse_fields(ev_draws, args.coarse_warm_tf, args.coarse_avg_tf)
+            X = np.stack([features_coarse(Ra, Pr, f) for (Ra, Pr, _), f in zip(tr, ftr)])
+            Xe = [features_coarse(Ra, Pr, f) for (Ra, Pr, _), f in zip(ev_draws, fev)]
+            ratio = (COARSE * COARSE) / float(args.fine * args.fine)
+            cost = [int(round(steps_c * ratio))] * len(ev_draws)
+            info = {"coarse_steps": steps_c, "coarse_cost_fine_steps": cost[0],
+                    "coarse_diverged_train": int(sum(bool(x) for x in sttr)),
+                    "coarse_diverged_eval": int(sum(bool(x) for x in stev))}
+        net = ConvNet(seed=0)
+        hist = train(net, X[keep], Y[keep], iters=args.iters)
+        starts[mode] = [predict(net, Ra, Pr, args.fine, x) for (Ra, Pr, _), x in zip(ev_draws, Xe)]
+        costs[mode] = cost
+        torch.cuda.synchronize()
+        res["inputs"][mode] = dict(info, loss=hist, seconds=time.time() - tm)
+    t2 = time.time()
+    ev, series = evaluate_starts(ev_draws, starts, args.run_tf, args.ref_tf, fine=args.fine, extra_cost=costs)
+    t3 = time.time()
+    res.update({"summary": summarize_starts(ev, modes), "eval": ev, "series": series,
+                "seconds": {"data": t1 - t0, "train": t2 - t1, "eval": t3 - t2}})
     if args.out:
         with open(args.out, "w") as fh:
             fh.write(json.dumps(res))
