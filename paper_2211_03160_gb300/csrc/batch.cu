@@ -251,6 +251,10 @@ cudaError_t batch_dispatch(bool launch, int dim, int prec, int vec, bool trt, co
     TLBM_BATCH_CASE(2, float, 1, 4, true)
     TLBM_BATCH_CASE(2, float, 1, 2, true)
     TLBM_BATCH_CASE(2, float, 1, 4, false)
+    TLBM_BATCH_CASE(2, __half, 2, 2, true)
+    TLBM_BATCH_CASE(2, __nv_bfloat16, 3, 2, true)
+    TLBM_BATCH_ROWS_CASE(2, __half, 2, 2, 2)
+    TLBM_BATCH_ROWS_CASE(2, __nv_bfloat16, 3, 2, 2)
     TLBM_BATCH_CASE(2, __half, 2, 4, true)
     TLBM_BATCH_CASE(2, __half, 2, 8, true)
     TLBM_BATCH_CASE(2, __half, 2, 8, false)
