@@ -359,19 +359,33 @@ TLBM_API void tlbm_batch_destroy(tlbm_batch_t b);
  * `stream` (a cudaStream_t, NULL = legacy stream) and returns TLBM_ERR_ARG for
  * bad shapes or NULL pointers. */
 
-/* FP32 weights w[cout][cin][3][3] -> BF16 GEMM operand a[cout][Kp],
- * Kp = 16 * ceil(9 cin / 16), zero-padded. */
+/* Elements (BF16) of the packed weight operand of a layer with cin input
+ * channels: 4608 * ceil(cin / 16); 0 for cin outside 1..32. */
+TLBM_API int tlbm_conv3x3_weight_elems(int cin);
+/* FP32 weights w[cout][cin][3][3] -> the BF16 tensor-core operand a of
+ * tlbm_conv3x3_weight_elems(cin) elements, in the tile order the forward
+ * kernel stages in shared memory: for tap t = 3 di + dj and 16-channel chunk
+ * h (CH = ceil(cin / 16) chunks), element
+ *   512 (t CH + h) + 256 (c' / 8) + 64 (m / 8) + 8 (m % 8) + c' % 8
+ * holds w[m][16 h + c'][di][dj], zero for m >= cout or 16 h + c' >= cin. */
 TLBM_API int tlbm_conv3x3_pack_weights(const float* w, int cout, int cin, void* a, void* stream);
 /* y[B][cout][H][W] (FP32) = bias + conv(x, w); x BF16 [B][cin][H][W]; a from
  * tlbm_conv3x3_pack_weights; bias FP32 [cout] or NULL; y_act (BF16, optional)
- * = relu(y) when relu != 0, else y. */
+ * = relu(y) when relu != 0, else y.  Runs as a tcgen05 implicit GEMM (128
+ * pixels x 32 channels per CTA, FP32 accumulator in tensor memory); a CTA whose
+ * MMAs do not complete within 0.5 s writes nothing and counts itself in
+ * tlbm_conv3x3_status. */
 TLBM_API int tlbm_conv3x3_forward(const void* x, const void* a, const float* bias, float* y, void* y_act, int B,
                                   int cin, int cout, int H, int W, int relu, void* stream);
 /* dx[B][cin][H][W] (FP32) = gradient w.r.t. the input of the convolution with
- * BF16 weights w_bf16[cout][cin][3][3], given dy (BF16 [B][cout][H][W]);
- * at_workspace: BF16 scratch of 32 * 288 elements. */
+ * BF16 weights w_bf16[cout][cin][3][3], given dy (BF16 [B][cout][H][W]): the
+ * same tensor-core kernel as the forward with the flipped, transposed weights
+ * (written to at_workspace, BF16 scratch of 32 * 288 elements). */
 TLBM_API int tlbm_conv3x3_backward_data(const void* dy, const void* w_bf16, float* dx, int B, int cin, int cout,
                                         int H, int W, void* at_workspace, void* stream);
+/* Number of forward / data-gradient CTAs since load that gave up waiting for
+ * their tensor-core MMAs (0 in a healthy run); synchronous. */
+TLBM_API int tlbm_conv3x3_status(unsigned long long* timeouts);
 /* Bytes of workspace tlbm_conv3x3_backward_weight needs for this shape. */
 TLBM_API int tlbm_conv3x3_workspace_bytes(int B, int cin, int cout, int H, int W, size_t* bytes);
 /* dw[cout][cin][3][3] (FP32) = sum over pixels of dy * patches(x), summed in a

@@ -1,13 +1,16 @@
 // Learned warm start: the layers of a small 3x3 convolutional network and the
 // pieces of its training loop, as CUDA kernels behind the C ABI.
 //
-// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16
-// operands, FP32 accumulation):
+// Convolutions are implicit GEMMs on the tensor cores, BF16 operands with FP32
+// accumulation:
 //   forward   out[b][m][p] = bias[m] + sum_k A[m][k] col(x)[k][b, p]
-//             with A = W reshaped to [Cout][Cin*9] and col(x) the 3x3 patches;
+//             with A = W reshaped to [Cout][Cin*9] and col(x) the 3x3 patches,
+//             on the 5th-generation tensor cores (tcgen05.mma, accumulator in
+//             tensor memory);
 //   data grad the same kernel with A = W transposed and flipped, x = dL/dy;
 //   weight grad  dW[m][n] = sum_{b,p} dy[b][m][p] col(x)[n][b, p], split over
-//             pixel ranges and summed in a fixed order (deterministic).
+//             pixel ranges and summed in a fixed order (deterministic), on the
+//             warp-level mma.sync m16n8k16.
 // Layout: NCHW, 3x3 kernel, stride 1, zero padding 1.  Channel counts up to 32.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -52,81 +55,243 @@ __device__ __forceinline__ bf16 patch(const bf16* __restrict__ x, int k, int K, 
     return x[(((long long)b * C + c) * H + ii) * W + jj];
 }
 
-// out[b][m][p] (FP32) = bias[m] + sum_k A[m][k] * patch(x)[k][b, p];
-// A: BF16 [M][Kp], zero for k >= K = C*9, Kp a multiple of 16, M <= 32.
-// out_act (optional, BF16) = relu(out) if relu else out.
-__global__ void __launch_bounds__(CONV_THREADS) conv3x3_igemm_kernel(const bf16* __restrict__ A, int M, int Kp,
-                                                                     const bf16* __restrict__ x, int B, int C,
-                                                                     int H, int W, const float* __restrict__ bias,
-                                                                     int relu, float* __restrict__ out,
-                                                                     bf16* __restrict__ out_act) {
-    extern __shared__ uint32_t sA[];  // MAX_ROWS x Kp BF16 as 32-bit pairs
-    const int words = MAX_ROWS * Kp / 2;
-    const uint32_t* A32 = reinterpret_cast<const uint32_t*>(A);
-    for (int w = threadIdx.x; w < words; w += CONV_THREADS) sA[w] = (w < M * Kp / 2) ? A32[w] : 0u;
-    __syncthreads();
+// ------------------------------------------------------------------ tcgen05 forward
+//
+// D[pixel][m] = bias[m] + sum_{c, di, dj} x[c][pixel + (di - 1, dj - 1)] A[m][9c + 3di + dj]
+// on the 5th-generation tensor cores: tcgen05.mma, cta_group::1, kind::f16 (BF16
+// in, FP32 accumulator in 32 columns of tensor memory), M = 128 pixels, N = 32
+// output channels (zero-padded), K = 16 input channels per instruction.
+//
+// Pixels are walked in a padded "virtual" layout.  The image is cut into
+// column strips of Wt = min(W, 126) columns; a strip with one halo column on
+// either side is a virtual image of width Wv = Wt + 2, whose position
+// v = (i + 1) Wv + (jj + 1) holds row i and strip column jj (image column
+// j = s Wt + jj).  There the 3x3 neighbour (di - 1, dj - 1) of position v is
+// v + (di - 1) Wv + (dj - 1), a constant shift.  A tile is the 128 positions
+// v0 .. v0 + 127 (v0 = Wv + 128 t); the CTA stages positions v0 - Wv - 1 ..
+// v0 + 128 + Wv of the input in shared memory channel-contiguous: position r
+// of channel group g (channels 8g .. 8g + 7, zero past C) is the 16 bytes at
+// sX + g PLANE + 16 r.  Read as a K-major operand whose core matrices are 8
+// consecutive positions x 8 channels (row step 16 bytes, step between 8-row
+// groups 128 bytes, step between the two K-adjacent channel groups PLANE), the
+// patch rows of tap (di, dj) are the same bytes from row di Wv + dj on, so the
+// layer is 9 x ceil(C / 16) MMAs per tile with no patch matrix built.  The
+// halo columns' outputs (jj = -1 or Wt) are computed and dropped.
+//
+// Shared-memory operands are unswizzled, in 8-row x 16-byte core matrices.
+// Matrix descriptor: start address >> 4 (bits 0-13), the byte step between
+// K-adjacent core matrices >> 4 (16-29), the step between 8-row groups >> 4
+// (32-45), descriptor version 1 (46-47), no swizzle (61-63 = 0).  Instruction
+// descriptor: FP32 accumulator (bits 4-5 = 1), BF16 A and B (7-9, 10-12 = 1),
+// both K-major (15, 16 = 0), N / 8 (17-22), M / 16 (24-28).  (Layouts checked
+// on the GPU against a CPU product of one 128 x 32 x 16 tile before this
+// kernel was written.)  The weights for tap t and channel chunk h (16
+// channels) are a 32 x 16 K-major tile at sW + 1024 (t CH + h): core matrix
+// (rows 8a.., channels 8e..) at 512 e + 128 a.  The packed weight operand in
+// global memory is that image byte for byte, so staging it is a plain copy.
+//
+// The kernel is persistent: a CTA stages the weights once, then loops over
+// tiles: stage the input tile, issue the MMAs from one thread, wait for their
+// commit on an mbarrier (bounded), read the accumulator back with tcgen05.ld
+// (warp w reads tensor-memory lanes 32w .. 32w + 31, i.e. its own 32
+// positions) and store.
+constexpr int TC_PIX = 128;        // output positions per tile (the MMA's M)
+constexpr int TC_N = 32;           // output channels, zero-padded (the MMA's N)
+constexpr int TC_WT = TC_PIX - 2;  // widest strip: its virtual row is one tile
+constexpr int TC_BATCH = 4;        // input-tile items a thread loads before storing them
+constexpr unsigned long long TC_WAIT_NS = 500000000;  // give up on the MMAs' completion after 0.5 s
+__device__ unsigned long long g_conv_timeouts;        // CTAs that gave up (tlbm_conv3x3_status)
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int K = C * 9;
-    const long long HW = (long long)H * W, P = (long long)B * HW;
-    const long long pbase = (long long)blockIdx.x * CONV_THREADS + warp * 32;
-    int pb[4], pi[4], pj[4];
-    bool pok[4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const long long q = pbase + nt * 8 + g;
-        pok[nt] = q < P;
-        const long long qq = pok[nt] ? q : 0;
-        pb[nt] = (int)(qq / HW);
-        const long long r = qq - (long long)pb[nt] * HW;
-        pi[nt] = (int)(r / W);
-        pj[nt] = (int)(r - (long long)pi[nt] * W);
-    }
-    float acc[2][4][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+__device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t k_step, uint32_t row_step) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((k_step >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((row_step >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
 
-    for (int k0 = 0; k0 < Kp; k0 += 16) {
-        uint32_t a[2][4];
+struct TcGeom {
+    int Wt, Wv, strips, tps;  // strip width, virtual width, strips per image, tiles per strip
+    long long tiles;          // B x strips x tps
+};
+
+__host__ __device__ inline int tc_rows(int Wv) { return TC_PIX + 2 * Wv + 2; }
+__host__ __device__ inline size_t tc_smem_bytes(int C, int Wv) {
+    const int CH = (C + 15) / 16;
+    return (size_t)9 * CH * 1024 + (size_t)2 * CH * tc_rows(Wv) * 16 + 16;
+}
+
+// out[b][m][i][j] (FP32) = bias[m] + conv; A: the 9 x CH weight tiles in the
+// order they take in shared memory (pack_weights_kernel), M <= 32, C <= 32;
+// out_act (optional, BF16) = relu(out) if relu else out.  Dynamic shared
+// memory: tc_smem_bytes(C, Wv).
+__global__ void __launch_bounds__(TC_PIX) conv3x3_tc_kernel(const bf16* __restrict__ A, int M,
+                                                            const bf16* __restrict__ x, int C, int H, int W,
+                                                            const float* __restrict__ bias, int relu,
+                                                            float* __restrict__ out, bf16* __restrict__ out_act,
+                                                            TcGeom geo) {
+    extern __shared__ __align__(1024) uint8_t tc_sm[];
+    const int CH = (C + 15) / 16, G = 2 * CH;
+    const int Wt = geo.Wt, Wv = geo.Wv;
+    const int rows = tc_rows(Wv), plane = rows * 16;
+    uint8_t* sW = tc_sm;
+    uint8_t* sX = tc_sm + 9 * CH * 1024;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sX + (size_t)G * plane);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const bf16 zero = __float2bfloat16_rn(0.f);
+
+    // weights, once: a straight copy of 9 x CH KB (at most 9 pieces of 16
+    // bytes per thread, all loads issued before the stores)
+    {
+        const int nw = 9 * CH * 64;
+        uint4 v[9];
+        if ((reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+            const uint4* A4 = reinterpret_cast<const uint4*>(A);
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int r0 = mt * 16 + g;
-            a[mt][0] = sA[(r0 * Kp + k0 + 2 * t) >> 1];
-            a[mt][1] = sA[((r0 + 8) * Kp + k0 + 2 * t) >> 1];
-            a[mt][2] = sA[(r0 * Kp + k0 + 2 * t + 8) >> 1];
-            a[mt][3] = sA[((r0 + 8) * Kp + k0 + 2 * t + 8) >> 1];
-        }
-        const int kb = k0 + 2 * t;
+            for (int u = 0; u < 9; ++u)
+                if (tid + u * TC_PIX < nw) v[u] = A4[tid + u * TC_PIX];
+        } else {
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const uint32_t b0 = pack2(patch(x, kb, K, pb[nt], pi[nt], pj[nt], C, H, W, pok[nt]),
-                                      patch(x, kb + 1, K, pb[nt], pi[nt], pj[nt], C, H, W, pok[nt]));
-            const uint32_t b1 = pack2(patch(x, kb + 8, K, pb[nt], pi[nt], pj[nt], C, H, W, pok[nt]),
-                                      patch(x, kb + 9, K, pb[nt], pi[nt], pj[nt], C, H, W, pok[nt]));
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], a[mt], b0, b1);
-        }
-    }
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int m = mt * 16 + g + (e >= 2 ? 8 : 0);
-                const long long q = pbase + nt * 8 + 2 * t + (e & 1);
-                if (m >= M || q >= P) continue;
-                const long long b = q / HW, p = q - b * HW;
-                const float v = acc[mt][nt][e] + (bias ? bias[m] : 0.f);
-                const long long o = (b * M + m) * HW + p;
-                out[o] = v;
-                if (out_act) out_act[o] = __float2bfloat16_rn(relu ? fmaxf(v, 0.f) : v);
+            for (int u = 0; u < 9; ++u) {
+                const bf16* src = A + 8 * (tid + u * TC_PIX);
+                if (tid + u * TC_PIX < nw)
+                    v[u] = make_uint4(pack2(src[0], src[1]), pack2(src[2], src[3]), pack2(src[4], src[5]),
+                                      pack2(src[6], src[7]));
             }
+        }
+#pragma unroll
+        for (int u = 0; u < 9; ++u)
+            if (tid + u * TC_PIX < nw) reinterpret_cast<uint4*>(sW)[tid + u * TC_PIX] = v[u];
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(tc_smem(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = *tslot;
+    const uint32_t idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_PIX >> 4) << 24);
+    const long long HW = (long long)H * W;
+
+    uint32_t it = 0;
+    for (long long tile = blockIdx.x; tile < geo.tiles; tile += gridDim.x, ++it) {
+        const long long bs = tile / geo.tps;
+        const int k = (int)(tile - bs * geo.tps);
+        const int b = (int)(bs / geo.strips), s = (int)(bs - (long long)b * geo.strips);
+        const int v0 = Wv + k * TC_PIX, vlo = v0 - Wv - 1;
+        const bf16* xb = x + (long long)b * C * HW;
+        // input tile: item (g, r) = 8 channels of virtual position vlo + r;
+        // TC_BATCH items per thread in flight before their stores
+        for (int e0 = 0; e0 < G * rows; e0 += TC_BATCH * TC_PIX) {
+            uint32_t w4[TC_BATCH][4];
+#pragma unroll
+            for (int u = 0; u < TC_BATCH; ++u) {
+                const int e = e0 + u * TC_PIX + tid;
+                const int g = e / rows, r = e - g * rows;
+                const int v = vlo + r;
+                w4[u][0] = w4[u][1] = w4[u][2] = w4[u][3] = 0u;
+                if (e < G * rows && v >= 0 && 8 * g < C) {
+                    const int i = v / Wv - 1, jj = v - (i + 1) * Wv - 1;
+                    const int j = s * Wt + jj;
+                    if (i >= 0 && i < H && j >= 0 && j < W) {
+                        const bf16* p = xb + (long long)(8 * g) * HW + (long long)i * W + j;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c0 = 8 * g + 2 * q;
+                            w4[u][q] = pack2(c0 < C ? p[(2 * q) * HW] : zero,
+                                             c0 + 1 < C ? p[(2 * q + 1) * HW] : zero);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TC_BATCH; ++u) {
+                const int e = e0 + u * TC_PIX + tid;
+                const int g = e / rows, r = e - g * rows;
+                if (e < G * rows)
+                    *reinterpret_cast<uint4*>(sX + g * plane + r * 16) =
+                        make_uint4(w4[u][0], w4[u][1], w4[u][2], w4[u][3]);
+            }
+        }
+        // the tile written by this CTA's threads becomes visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t x0 = tc_smem(sX), w0 = tc_smem(sW);
+            for (int t = 0; t < 9; ++t) {
+                const int shift = (t / 3) * Wv + (t % 3);
+                for (int h = 0; h < CH; ++h) {
+                    const uint64_t ad = tc_desc(x0 + 2 * h * plane + shift * 16, plane, 128);
+                    const uint64_t bd = tc_desc(w0 + (t * CH + h) * 1024, 512, 128);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"((uint32_t)(t + h > 0))
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tc_smem(bar))
+                         : "memory");
+        }
+        // bounded wait for this tile's MMAs (phase `it` of the barrier)
+        uint32_t done = 0;
+        unsigned long long t0, t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        while (!done) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(tc_smem(bar)), "r"(it & 1u)
+                : "memory");
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+            if (!done && t1 - t0 > TC_WAIT_NS) break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int failed = __syncthreads_or(!done);
+        if (!failed) {
+            uint32_t r[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                "[%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr + ((uint32_t)(32 * warp) << 16)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int v = v0 + tid;
+            const int i = v / Wv - 1, jj = v - (i + 1) * Wv - 1, j = s * Wt + jj;
+            if (i < H && jj >= 0 && jj < Wt && j < W) {
+                const long long o0 = (long long)b * M * HW + (long long)i * W + j;
+#pragma unroll
+                for (int m = 0; m < TC_N; ++m) {
+                    if (m < M) {
+                        const float y = __uint_as_float(r[m]) + (bias ? bias[m] : 0.f);
+                        out[o0 + m * HW] = y;
+                        if (out_act) out_act[o0 + m * HW] = __float2bfloat16_rn(relu ? fmaxf(y, 0.f) : y);
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (failed) {
+            if (tid == 0) atomicAdd(&g_conv_timeouts, 1ull);
+            break;
+        }
+    }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(taddr) : "memory");
 }
 
 // Weight gradient partials: part[s][m][n] = sum over pixels q in split s of
@@ -232,25 +397,38 @@ __global__ void bias_grad_kernel(const float* __restrict__ dy, int B, int M, lon
     if (threadIdx.x == 0) db[m] = sm[0];
 }
 
-// At[c][o*9 + di*3 + dj] = W[o][c][2-di][2-dj], zero-padded to Kp columns.
-__global__ void flip_transpose_kernel(const bf16* __restrict__ w, int O, int C, int Kp, bf16* __restrict__ at) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= C * Kp) return;
-    const int c = idx / Kp, k = idx - c * Kp;
-    if (k >= O * 9) {
-        at[idx] = __float2bfloat16_rn(0.f);
-        return;
-    }
-    const int o = k / 9, r = k - 9 * o, di = r / 3, dj = r % 3;
-    at[idx] = w[((o * C + c) * 3 + (2 - di)) * 3 + (2 - dj)];
+// Element idx of the tensor-core weight operand (tile order of
+// conv3x3_tc_kernel's shared memory): (tap t, chunk h, output row m, input
+// channel c) with idx = 512 (t CH + h) + 256 (c' / 8) + 64 (m / 8) + 8 (m % 8)
+// + c' % 8, c = 16 h + c'.
+struct TapIndex {
+    int t, m, c;
+};
+__device__ __forceinline__ TapIndex tap_index(int idx, int CH) {
+    const int th = idx >> 9, e = idx & 511;
+    const int t = th / CH, h = th - t * CH;
+    return {t, 8 * ((e >> 6) & 3) + ((e >> 3) & 7), 16 * h + 8 * (e >> 8) + (e & 7)};
 }
 
-// W [O][C][3][3] (FP32 master) -> A [O][Kp] BF16, zero-padded.
-__global__ void pack_weights_kernel(const float* __restrict__ w, int O, int C, int Kp, bf16* __restrict__ a) {
+// Data-gradient operand: At(t, m = input channel, c = output channel)
+// = W[c][m][2 - di][2 - dj] (t = 3 di + dj), zero where m >= M or c >= C.
+__global__ void flip_transpose_kernel(const bf16* __restrict__ w, int C, int M, bf16* __restrict__ at) {
+    const int CH = (C + 15) / 16;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= O * Kp) return;
-    const int o = idx / Kp, k = idx - o * Kp;
-    a[idx] = __float2bfloat16_rn(k < C * 9 ? w[o * C * 9 + k] : 0.f);
+    if (idx >= 9 * CH * 512) return;
+    const TapIndex q = tap_index(idx, CH);
+    at[idx] = (q.m < M && q.c < C) ? w[((q.c * M + q.m) * 3 + (2 - q.t / 3)) * 3 + (2 - q.t % 3)]
+                                   : __float2bfloat16_rn(0.f);
+}
+
+// Forward operand: A(t, m, c) = W[m][c][di][dj] (FP32 master -> BF16), zero
+// where m >= O or c >= C.
+__global__ void pack_weights_kernel(const float* __restrict__ w, int O, int C, bf16* __restrict__ a) {
+    const int CH = (C + 15) / 16;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 9 * CH * 512) return;
+    const TapIndex q = tap_index(idx, CH);
+    a[idx] = __float2bfloat16_rn((q.m < O && q.c < C) ? w[(q.m * C + q.c) * 9 + q.t] : 0.f);
 }
 
 __global__ void relu_backward_kernel(const float* __restrict__ dx, const float* __restrict__ y, long long n,
@@ -339,45 +517,69 @@ int status_of(cudaError_t e) { return e == cudaSuccess ? TLBM_OK : TLBM_ERR_CUDA
 
 bool conv_shape_ok(int B, int C, int M, int H, int W) {
     return B > 0 && C > 0 && C <= 32 && M > 0 && M <= MAX_ROWS && H > 0 && W > 0 &&
-           (long long)B * H * W < (1ll << 40);
+           (long long)B * H * W < (1ll << 40) && (long long)H * TC_PIX < (1ll << 30);
+}
+
+// Persistent launch: as many CTAs as fit the SMs at once (about 43 KB of
+// shared memory each at 32 channels), never more than there are tiles.
+int launch_tc(const bf16* A, int M, const bf16* x, int B, int C, int H, int W, const float* bias, int relu,
+              float* out, bf16* out_act, cudaStream_t s) {
+    TcGeom geo;
+    geo.Wt = W < TC_WT ? W : TC_WT;
+    geo.Wv = geo.Wt + 2;
+    geo.strips = (W + geo.Wt - 1) / geo.Wt;
+    geo.tps = (int)(((long long)H * geo.Wv + TC_PIX - 1) / TC_PIX);
+    geo.tiles = (long long)B * geo.strips * geo.tps;
+    const size_t smem = tc_smem_bytes(C, geo.Wv);
+    // CTAs resident per SM: as many as shared memory holds (228 KB per SM,
+    // 1 KB reserved per CTA), at most 8 (each holds 32 of the SM's 512
+    // tensor-memory columns); launched with the largest shared-memory carveout.
+    static const cudaError_t carve = cudaFuncSetAttribute(
+        conv3x3_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    int dev = 0, sms = 0;
+    if (carve != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return TLBM_ERR_CUDA;
+    long long per = (long long)(228 * 1024) / (long long)(smem + 1024);
+    per = per < 1 ? 1 : (per > 8 ? 8 : per);
+    const long long grid = geo.tiles < sms * per ? geo.tiles : sms * per;
+    conv3x3_tc_kernel<<<(unsigned)grid, TC_PIX, smem, s>>>(A, M, x, C, H, W, bias, relu, out, out_act, geo);
+    return status_of(cudaGetLastError());
 }
 
 }  // namespace
 
 extern "C" int tlbm_conv3x3_pack_weights(const float* w, int cout, int cin, void* a, void* stream) {
     if (!w || !a || cout < 1 || cout > MAX_ROWS || cin < 1 || cin > 32) return TLBM_ERR_ARG;
-    const int Kp = (cin * 9 + 15) / 16 * 16;
-    pack_weights_kernel<<<grid_for((long long)cout * Kp, 256), 256, 0, (cudaStream_t)stream>>>(w, cout, cin, Kp,
-                                                                                            (bf16*)a);
+    const int n = 9 * 512 * ((cin + 15) / 16);
+    pack_weights_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(w, cout, cin, (bf16*)a);
     return status_of(cudaGetLastError());
 }
 
 extern "C" int tlbm_conv3x3_forward(const void* x, const void* a, const float* bias, float* y, void* y_act,
                                     int B, int cin, int cout, int H, int W, int relu, void* stream) {
     if (!x || !a || !y || !conv_shape_ok(B, cin, cout, H, W)) return TLBM_ERR_ARG;
-    const int Kp = (cin * 9 + 15) / 16 * 16;
-    const long long P = (long long)B * H * W;
-    const size_t smem = (size_t)MAX_ROWS * Kp * sizeof(bf16);
-    conv3x3_igemm_kernel<<<(unsigned)((P + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, smem,
-                           (cudaStream_t)stream>>>((const bf16*)a, cout, Kp, (const bf16*)x, B, cin, H, W, bias, relu,
-                                                   y, (bf16*)y_act);
-    return status_of(cudaGetLastError());
+    return launch_tc((const bf16*)a, cout, (const bf16*)x, B, cin, H, W, bias, relu, y, (bf16*)y_act,
+                     (cudaStream_t)stream);
 }
 
 extern "C" int tlbm_conv3x3_backward_data(const void* dy, const void* w_bf16, float* dx, int B, int cin, int cout,
                                           int H, int W, void* at_workspace, void* stream) {
     if (!dy || !w_bf16 || !dx || !at_workspace || !conv_shape_ok(B, cout, cin, H, W)) return TLBM_ERR_ARG;
-    const int Kp = (cout * 9 + 15) / 16 * 16;
-    flip_transpose_kernel<<<grid_for((long long)cin * Kp, 256), 256, 0, (cudaStream_t)stream>>>(
-        (const bf16*)w_bf16, cout, cin, Kp, (bf16*)at_workspace);
+    const int n = 9 * 512 * ((cout + 15) / 16);
+    flip_transpose_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16*)w_bf16, cout, cin,
+                                                                             (bf16*)at_workspace);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return TLBM_ERR_CUDA;
-    const long long P = (long long)B * H * W;
-    const size_t smem = (size_t)MAX_ROWS * Kp * sizeof(bf16);
-    conv3x3_igemm_kernel<<<(unsigned)((P + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, smem,
-                           (cudaStream_t)stream>>>((const bf16*)at_workspace, cin, Kp, (const bf16*)dy, B, cout, H,
-                                                   W, nullptr, 0, dx, nullptr);
-    return status_of(cudaGetLastError());
+    return launch_tc((const bf16*)at_workspace, cin, (const bf16*)dy, B, cout, H, W, nullptr, 0, dx, nullptr,
+                     (cudaStream_t)stream);
+}
+
+extern "C" int tlbm_conv3x3_weight_elems(int cin) { return cin < 1 || cin > 32 ? 0 : 9 * 512 * ((cin + 15) / 16); }
+
+extern "C" int tlbm_conv3x3_status(unsigned long long* timeouts) {
+    if (!timeouts) return TLBM_ERR_ARG;
+    return status_of(cudaMemcpyFromSymbol(timeouts, g_conv_timeouts, sizeof(unsigned long long)));
 }
 
 extern "C" int tlbm_conv3x3_workspace_bytes(int B, int cin, int cout, int H, int W, size_t* bytes) {

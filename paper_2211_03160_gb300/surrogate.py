@@ -135,8 +135,7 @@ class ConvNet:
                 w *= 0.1
             self.w.append(w)
             self.b.append(torch.zeros(cout, dtype=torch.float32, device=device))
-            kp = (cin * 9 + 15) // 16 * 16
-            self.a.append(torch.empty((cout, kp), dtype=torch.bfloat16, device=device))
+            self.a.append(torch.empty(tlbm.tlbm_conv3x3_weight_elems(cin), dtype=torch.bfloat16, device=device))
             self.mw.append(torch.zeros_like(w))
             self.vw.append(torch.zeros_like(w))
             self.mb.append(torch.zeros(cout, dtype=torch.float32, device=device))
@@ -471,6 +470,58 @@ def summarize(ev) -> dict:
     return res
 
 
+def time_layers(batch: int = 48, n: int = COARSE, reps: int = 20, warmup: int = 3):
+    """CUDA-event timings (ms per call, median over reps) of the 32 -> 32
+    channel layer at the training batch: forward (tcgen05), data gradient
+    (tcgen05) and weight gradient (mma.sync), each with the FLOPs of its GEMM
+    (2 x pixels x 32 x 288) as TFLOP/s and its compulsory HBM bytes as GB/s."""
+    import torch
+
+    s = torch.cuda.current_stream()
+    B, C, M = batch, WIDTH, WIDTH
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = (torch.rand((B, C, n, n), generator=g) * 2 - 1).to(torch.bfloat16).cuda()
+    w = ((torch.rand((M, C, 3, 3), generator=g) * 2 - 1) * 0.1).cuda()
+    bias = torch.zeros(M, dtype=torch.float32, device="cuda")
+    a = torch.empty(tlbm.tlbm_conv3x3_weight_elems(C), dtype=torch.bfloat16, device="cuda")
+    tlbm.tlbm_conv3x3_pack_weights(w, M, C, a, s)
+    w16 = w.to(torch.bfloat16)
+    y = torch.empty((B, M, n, n), dtype=torch.float32, device="cuda")
+    act = torch.empty((B, M, n, n), dtype=torch.bfloat16, device="cuda")
+    dy32 = torch.empty_like(y).uniform_(-1, 1)
+    dy16 = dy32.to(torch.bfloat16)
+    dx = torch.empty((B, C, n, n), dtype=torch.float32, device="cuda")
+    at = torch.empty(32 * 288, dtype=torch.bfloat16, device="cuda")
+    ws = torch.empty(tlbm.tlbm_conv3x3_workspace_bytes(B, C, M, n, n), dtype=torch.uint8, device="cuda")
+    dw = torch.empty((M, C, 3, 3), dtype=torch.float32, device="cuda")
+    db = torch.empty(M, dtype=torch.float32, device="cuda")
+    ops = {
+        "forward": (lambda: tlbm.tlbm_conv3x3_forward(x, a, bias, y, act, B, C, M, n, n, 1, s),
+                    x.numel() * 2 + y.numel() * 6),
+        "backward_data": (lambda: tlbm.tlbm_conv3x3_backward_data(dy16, w16, dx, B, C, M, n, n, at, s),
+                          dy16.numel() * 2 + dx.numel() * 4),
+        "backward_weight": (lambda: tlbm.tlbm_conv3x3_backward_weight(x, dy16, dy32, dw, db, B, C, M, n, n, ws, s),
+                            x.numel() * 2 + dy16.numel() * 2 + dy32.numel() * 4),
+    }
+    flops = 2.0 * B * n * n * M * C * 9
+    out = {"batch": B, "n": n, "cin": C, "cout": M, "gemm_flops": flops}
+    for name, (fn, nbytes) in ops.items():
+        for _ in range(warmup):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        out[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12, "gbs": nbytes / (ms * 1e-3) / 1e9}
+    out["timeouts"] = tlbm.tlbm_conv3x3_status()
+    return out
+
+
 def main(argv=None):
     import torch
 
@@ -491,8 +542,13 @@ def main(argv=None):
     ap.add_argument("--out", default="", help="write the full result (per-draw steps and Nu series), JSON")
     ap.add_argument("--save-data", default="", help="write the generated training targets (.npz)")
     ap.add_argument("--load-data", default="", help="reuse training targets written by --save-data")
+    ap.add_argument("--time-layers", action="store_true",
+                    help="only time the 32-channel layer's forward and gradients at the training batch, JSON")
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
+    if args.time_layers:
+        print(json.dumps(time_layers(batch=args.train_draws)))
+        return 0
     t0 = time.time()
     tr = draws(args.train_draws, seed=1, log_ra=tuple(args.log_ra))
     ev_draws = draws(args.eval_draws, seed=2, log_ra=tuple(args.log_ra))

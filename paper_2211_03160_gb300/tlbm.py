@@ -97,6 +97,8 @@ _SIGS = {
                                        C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "tlbm_conv3x3_backward_data": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                              C.c_int, C.c_void_p, C.c_void_p]),
+    "tlbm_conv3x3_status": (C.c_int, [C.POINTER(C.c_ulonglong)]),
+    "tlbm_conv3x3_weight_elems": (C.c_int, [C.c_int]),
     "tlbm_conv3x3_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "tlbm_conv3x3_backward_weight": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                                C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
@@ -301,6 +303,16 @@ def tlbm_conv3x3_forward(x, a, bias, y, y_act, B, cin, cout, H, W, relu, stream=
 def tlbm_conv3x3_backward_data(dy, w_bf16, dx, B, cin, cout, H, W, at_workspace, stream=None):
     _c(lib().tlbm_conv3x3_backward_data(_ptr(dy), _ptr(w_bf16), _ptr(dx), B, cin, cout, H, W, _ptr(at_workspace),
                                         _cs(stream)))
+
+
+def tlbm_conv3x3_weight_elems(cin: int) -> int:
+    return int(lib().tlbm_conv3x3_weight_elems(cin))
+
+
+def tlbm_conv3x3_status() -> int:
+    n = C.c_ulonglong()
+    _c(lib().tlbm_conv3x3_status(C.byref(n)))
+    return n.value
 
 
 def tlbm_conv3x3_workspace_bytes(B, cin, cout, H, W) -> int:

@@ -35,7 +35,8 @@ def _np(t):
     return t.float().cpu().numpy().astype(np.float64) if t.dtype == torch.bfloat16 else t.cpu().numpy().astype(np.float64)
 
 
-SHAPES = [(2, 5, 32, 13, 11), (3, 32, 32, 9, 17), (1, 32, 3, 65, 65), (2, 7, 5, 4, 3)]
+SHAPES = [(2, 5, 32, 13, 11), (3, 32, 32, 9, 17), (1, 32, 3, 65, 65), (2, 7, 5, 4, 3), (1, 17, 9, 5, 260),
+          (2, 3, 2, 3, 127)]
 
 
 @pytest.mark.parametrize("B,cin,cout,H,W", SHAPES)
@@ -46,8 +47,7 @@ def test_conv_forward_backward_match_oracle(T, B, cin, cout, H, W):
     x = _bf16(inputs.uniform_array(1 + cin, (B, cin, H, W), -1, 1)).cuda()
     w32 = torch.tensor(inputs.uniform_array(2 + cin, (cout, cin, 3, 3), -0.3, 0.3), dtype=torch.float32).cuda()
     bias = torch.tensor(inputs.uniform_array(3, (cout,), -0.1, 0.1), dtype=torch.float32).cuda()
-    kp = (cin * 9 + 15) // 16 * 16
-    a = torch.empty((cout, kp), dtype=torch.bfloat16, device="cuda")
+    a = torch.empty(T.tlbm_conv3x3_weight_elems(cin), dtype=torch.bfloat16, device="cuda")
     T.tlbm_conv3x3_pack_weights(w32, cout, cin, a, s)
     w16 = w32.to(torch.bfloat16)
     y = torch.empty((B, cout, H, W), dtype=torch.float32, device="cuda")
@@ -77,6 +77,89 @@ def test_conv_forward_backward_match_oracle(T, B, cin, cout, H, W):
     dw2 = torch.empty_like(dw)
     T.tlbm_conv3x3_backward_weight(x, dy16, dy32, dw2, db, B, cin, cout, H, W, ws, s)
     assert torch.equal(dw, dw2)
+    assert T.tlbm_conv3x3_status() == 0
+
+
+def test_conv_training_batch_sampled_images_match_oracle(T):
+    """The 32 -> 32 layer at the training batch (48 x 65 x 65 = 1585 CTAs of
+    128 pixels, ragged last tile): the images are independent, so three of
+    them are checked against the oracle run on that image alone."""
+    import torch
+
+    B, cin, cout, H, W = 48, 32, 32, 65, 65
+    s = torch.cuda.current_stream()
+    x = _bf16(inputs.uniform_array(11, (B, cin, H, W), -1, 1)).cuda()
+    w32 = torch.tensor(inputs.uniform_array(12, (cout, cin, 3, 3), -0.1, 0.1), dtype=torch.float32).cuda()
+    bias = torch.tensor(inputs.uniform_array(13, (cout,), -0.1, 0.1), dtype=torch.float32).cuda()
+    a = torch.empty(T.tlbm_conv3x3_weight_elems(cin), dtype=torch.bfloat16, device="cuda")
+    T.tlbm_conv3x3_pack_weights(w32, cout, cin, a, s)
+    y = torch.empty((B, cout, H, W), dtype=torch.float32, device="cuda")
+    T.tlbm_conv3x3_forward(x, a, bias, y, None, B, cin, cout, H, W, 0, s)
+    dy16 = _bf16(inputs.uniform_array(14, (B, cout, H, W), -1, 1)).cuda()
+    dx = torch.empty((B, cin, H, W), dtype=torch.float32, device="cuda")
+    at = torch.empty(32 * 288, dtype=torch.bfloat16, device="cuda")
+    w16 = w32.to(torch.bfloat16)
+    T.tlbm_conv3x3_backward_data(dy16, w16, dx, B, cin, cout, H, W, at, s)
+    torch.cuda.synchronize()
+    assert T.tlbm_conv3x3_status() == 0
+    wr, yc, dxc = _np(w16), y.cpu().numpy(), dx.cpu().numpy()
+    for b in (0, 23, 47):
+        xr = _np(x[b:b + 1])
+        ref = CO.conv3x3(xr, wr, _np(bias))
+        assert np.abs(yc[b:b + 1] - ref).max() <= 1e-5 * np.abs(ref).max()
+        rdx, _, _ = CO.conv3x3_backward(xr, wr, _np(dy16[b:b + 1]))
+        assert np.abs(dxc[b:b + 1] - rdx).max() <= 1e-5 * np.abs(rdx).max()
+
+
+@pytest.mark.parametrize("cout,cin", [(32, 32), (3, 5), (9, 17)])
+def test_packed_weight_layout(T, cout, cin):
+    """The packed operand holds w[m][16h + c'][di][dj] at element
+    512 (t CH + h) + 256 (c' / 8) + 64 (m / 8) + 8 (m % 8) + c' % 8, zero
+    elsewhere (the documented tile order)."""
+    import torch
+
+    w32 = torch.tensor(inputs.uniform_array(31 + cin, (cout, cin, 3, 3), -1, 1), dtype=torch.float32).cuda()
+    n = T.tlbm_conv3x3_weight_elems(cin)
+    ch = (cin + 15) // 16
+    assert n == 4608 * ch
+    a = torch.full((n,), 7.0, dtype=torch.bfloat16, device="cuda")
+    T.tlbm_conv3x3_pack_weights(w32, cout, cin, a, torch.cuda.current_stream())
+    w16 = _np(w32.to(torch.bfloat16))
+    want = np.zeros(n)
+    for t in range(9):
+        for h in range(ch):
+            for m in range(cout):
+                for cp in range(16):
+                    c = 16 * h + cp
+                    if c < cin:
+                        want[512 * (t * ch + h) + 256 * (cp // 8) + 64 * (m // 8) + 8 * (m % 8) + cp % 8] = \
+                            w16[m, c, t // 3, t % 3]
+    assert np.array_equal(_np(a), want)
+
+
+def test_conv_forward_with_unaligned_weight_pointer(T):
+    """Weights that do not start on a 16-byte boundary take the element-wise
+    staging path and give the same bits as aligned ones."""
+    import torch
+
+    B, cin, cout, H, W = 2, 7, 5, 19, 23
+    s = torch.cuda.current_stream()
+    n = T.tlbm_conv3x3_weight_elems(cin)
+    x = _bf16(inputs.uniform_array(21, (B, cin, H, W), -1, 1)).cuda()
+    w32 = torch.tensor(inputs.uniform_array(22, (cout, cin, 3, 3), -0.3, 0.3), dtype=torch.float32).cuda()
+    a = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    T.tlbm_conv3x3_pack_weights(w32, cout, cin, a, s)
+    store = torch.empty(n + 1, dtype=torch.bfloat16, device="cuda")
+    store[1:] = a
+    a_odd = store[1:]
+    assert a_odd.data_ptr() % 16 != 0
+    y = torch.empty((B, cout, H, W), dtype=torch.float32, device="cuda")
+    y_odd = torch.empty_like(y)
+    T.tlbm_conv3x3_forward(x, a, None, y, None, B, cin, cout, H, W, 0, s)
+    T.tlbm_conv3x3_forward(x, a_odd, None, y_odd, None, B, cin, cout, H, W, 0, s)
+    assert torch.equal(y, y_odd)
+    ref = CO.conv3x3(_np(x), _np(w32.to(torch.bfloat16)), np.zeros(cout))
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
 def test_loss_relu_adam_upsample_match_oracle(T):
