@@ -383,13 +383,19 @@ TLBM_API int tlbm_conv3x3_forward(const void* x, const void* a, const float* bia
  * (written to at_workspace, BF16 scratch of 32 * 288 elements). */
 TLBM_API int tlbm_conv3x3_backward_data(const void* dy, const void* w_bf16, float* dx, int B, int cin, int cout,
                                         int H, int W, void* at_workspace, void* stream);
-/* Number of forward / data-gradient CTAs since load that gave up waiting for
- * their tensor-core MMAs (0 in a healthy run); synchronous. */
+/* Number of convolution CTAs (forward, data or weight gradient) since load that
+ * gave up waiting for their tensor-core MMAs (0 in a healthy run); synchronous. */
 TLBM_API int tlbm_conv3x3_status(unsigned long long* timeouts);
-/* Bytes of workspace tlbm_conv3x3_backward_weight needs for this shape. */
+/* Bytes of workspace tlbm_conv3x3_backward_weight needs for this shape on the
+ * current device (one FP32 partial of 32 x 288 per CTA of the persistent
+ * weight-gradient kernel, whose count follows the device's SM count). */
 TLBM_API int tlbm_conv3x3_workspace_bytes(int B, int cin, int cout, int H, int W, size_t* bytes);
 /* dw[cout][cin][3][3] (FP32) = sum over pixels of dy * patches(x), summed in a
- * fixed order; db[cout] = sum of dy (FP32 dy, optional).  x, dy_bf16: BF16. */
+ * fixed order (tcgen05 GEMMs per CTA, the CTAs' partials added in CTA order:
+ * the same bits on every call on a given device); db[cout] = sum of dy (FP32 dy,
+ * optional; two fixed-order levels).  x, dy_bf16: BF16.  A CTA whose MMAs do
+ * not complete within 0.5 s writes NaN partials and counts itself in
+ * tlbm_conv3x3_status. */
 TLBM_API int tlbm_conv3x3_backward_weight(const void* x, const void* dy_bf16, const float* dy, float* dw, float* db,
                                           int B, int cin, int cout, int H, int W, void* workspace,
                                           size_t workspace_bytes, void* stream);

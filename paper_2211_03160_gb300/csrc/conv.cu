@@ -8,9 +8,9 @@
 //             on the 5th-generation tensor cores (tcgen05.mma, accumulator in
 //             tensor memory);
 //   data grad the same kernel with A = W transposed and flipped, x = dL/dy;
-//   weight grad  dW[m][n] = sum_{b,p} dy[b][m][p] col(x)[n][b, p], split over
-//             pixel ranges and summed in a fixed order (deterministic), on the
-//             warp-level mma.sync m16n8k16.
+//   weight grad  dW[m][n] = sum_{b,p} dy[b][m][p] col(x)[n][b, p], per-CTA
+//             partials over tiles of pixels summed in a fixed order
+//             (deterministic), also on tcgen05.
 // Layout: NCHW, 3x3 kernel, stride 1, zero padding 1.  Channel counts up to 32.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -23,36 +23,10 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int CONV_THREADS = 128;     // 4 warps; each warp: 32 output rows x 32 pixels
-constexpr int MAX_ROWS = 32;          // output channels per GEMM (two 16-row tiles)
-constexpr int WG_SPLIT = 2048;        // pixels summed by one weight-gradient block
-constexpr int WG_NT = 9;              // 8-column tiles per warp in the weight gradient (36 = 288 / 8 per block)
+constexpr int MAX_ROWS = 32;          // output channels at most (the MMA's N)
 
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// D += A B for one 16x8x16 tile; fragment layouts as in the PTX ISA for
-// mma.m16n8k16 with .bf16 inputs (g = lane/4, t = lane%4):
-//   A regs: (g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..), (g+8, 2t+8..)
-//   B regs: (k = 2t..2t+1, n = g), (k = 2t+8.., n = g)
-//   D:      (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// One element of the 3x3 patch matrix: row k = c*9 + di*3 + dj, pixel (b, i, j).
-__device__ __forceinline__ bf16 patch(const bf16* __restrict__ x, int k, int K, int b, int i, int j, int C, int H,
-                                      int W, bool pix_ok) {
-    if (!pix_ok || k >= K) return __float2bfloat16_rn(0.f);
-    const int c = k / 9, r = k - 9 * c;
-    const int ii = i + r / 3 - 1, jj = j + r % 3 - 1;
-    if (ii < 0 || ii >= H || jj < 0 || jj >= W) return __float2bfloat16_rn(0.f);
-    return x[(((long long)b * C + c) * H + ii) * W + jj];
 }
 
 // ------------------------------------------------------------------ tcgen05 forward
@@ -98,7 +72,7 @@ __device__ __forceinline__ bf16 patch(const bf16* __restrict__ x, int k, int K, 
 constexpr int TC_PIX = 128;        // output positions per tile (the MMA's M)
 constexpr int TC_N = 32;           // output channels, zero-padded (the MMA's N)
 constexpr int TC_WT = TC_PIX - 2;  // widest strip: its virtual row is one tile
-constexpr int TC_BATCH = 4;        // input-tile items a thread loads before storing them
+constexpr int TC_BATCH = 8;        // input-tile items a thread loads before storing them
 constexpr unsigned long long TC_WAIT_NS = 500000000;  // give up on the MMAs' completion after 0.5 s
 __device__ unsigned long long g_conv_timeouts;        // CTAs that gave up (tlbm_conv3x3_status)
 
@@ -114,9 +88,18 @@ struct TcGeom {
 };
 
 __host__ __device__ inline int tc_rows(int Wv) { return TC_PIX + 2 * Wv + 2; }
+// weights, input tile, the tile's position table (int per row, padded to 16
+// bytes), mbarrier + tensor-memory address slot
 __host__ __device__ inline size_t tc_smem_bytes(int C, int Wv) {
     const int CH = (C + 15) / 16;
-    return (size_t)9 * CH * 1024 + (size_t)2 * CH * tc_rows(Wv) * 16 + 16;
+    return (size_t)9 * CH * 1024 + (size_t)2 * CH * tc_rows(Wv) * 16 + (size_t)(tc_rows(Wv) + 3) / 4 * 16 + 16;
+}
+
+// Image offset i W + j of virtual position v of strip s, or -1 outside the image.
+__device__ __forceinline__ int tc_offset(int v, int s, int Wt, int Wv, int H, int W) {
+    if (v < 0) return -1;
+    const int i = v / Wv - 1, jj = v - (i + 1) * Wv - 1, j = s * Wt + jj;
+    return (i >= 0 && i < H && j >= 0 && j < W) ? i * W + j : -1;
 }
 
 // out[b][m][i][j] (FP32) = bias[m] + conv; A: the 9 x CH weight tiles in the
@@ -134,9 +117,12 @@ __global__ void __launch_bounds__(TC_PIX) conv3x3_tc_kernel(const bf16* __restri
     const int rows = tc_rows(Wv), plane = rows * 16;
     uint8_t* sW = tc_sm;
     uint8_t* sX = tc_sm + 9 * CH * 1024;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sX + (size_t)G * plane);
+    int* xoff = reinterpret_cast<int*>(sX + (size_t)G * plane);  // image offset of each staged position
+    uint64_t* bar = reinterpret_cast<uint64_t*>(xoff + (rows + 3) / 4 * 4);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
+    // this thread's first input-tile item (g0, r0) and the step between its items
+    const int g0 = tid / rows, r0 = tid - g0 * rows, dg = TC_PIX / rows, dr = TC_PIX - dg * rows;
     const bf16 zero = __float2bfloat16_rn(0.f);
 
     // weights, once: a straight copy of 9 x CH KB (at most 9 pieces of 16
@@ -186,38 +172,41 @@ __global__ void __launch_bounds__(TC_PIX) conv3x3_tc_kernel(const bf16* __restri
         const int b = (int)(bs / geo.strips), s = (int)(bs - (long long)b * geo.strips);
         const int v0 = Wv + k * TC_PIX, vlo = v0 - Wv - 1;
         const bf16* xb = x + (long long)b * C * HW;
+        // position table for this tile (the previous tile's readers are past
+        // the barrier that ended their iteration)
+        for (int r = tid; r < rows; r += TC_PIX) xoff[r] = tc_offset(vlo + r, s, Wt, Wv, H, W);
+        __syncthreads();
         // input tile: item (g, r) = 8 channels of virtual position vlo + r;
         // TC_BATCH items per thread in flight before their stores
+        int g = g0, r = r0;
         for (int e0 = 0; e0 < G * rows; e0 += TC_BATCH * TC_PIX) {
             uint32_t w4[TC_BATCH][4];
+            int dst[TC_BATCH];
 #pragma unroll
             for (int u = 0; u < TC_BATCH; ++u) {
-                const int e = e0 + u * TC_PIX + tid;
-                const int g = e / rows, r = e - g * rows;
-                const int v = vlo + r;
+                const bool in = e0 + u * TC_PIX + tid < G * rows;
+                dst[u] = in ? g * plane + r * 16 : -1;
                 w4[u][0] = w4[u][1] = w4[u][2] = w4[u][3] = 0u;
-                if (e < G * rows && v >= 0 && 8 * g < C) {
-                    const int i = v / Wv - 1, jj = v - (i + 1) * Wv - 1;
-                    const int j = s * Wt + jj;
-                    if (i >= 0 && i < H && j >= 0 && j < W) {
-                        const bf16* p = xb + (long long)(8 * g) * HW + (long long)i * W + j;
+                const int o = (in && 8 * g < C) ? xoff[r] : -1;
+                if (o >= 0) {
+                    const bf16* p = xb + (long long)(8 * g) * HW + o;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int c0 = 8 * g + 2 * q;
-                            w4[u][q] = pack2(c0 < C ? p[(2 * q) * HW] : zero,
-                                             c0 + 1 < C ? p[(2 * q + 1) * HW] : zero);
-                        }
+                    for (int q = 0; q < 4; ++q) {
+                        const int c0 = 8 * g + 2 * q;
+                        w4[u][q] = pack2(c0 < C ? p[(2 * q) * HW] : zero, c0 + 1 < C ? p[(2 * q + 1) * HW] : zero);
                     }
+                }
+                r += dr;
+                g += dg;
+                if (r >= rows) {
+                    r -= rows;
+                    ++g;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < TC_BATCH; ++u) {
-                const int e = e0 + u * TC_PIX + tid;
-                const int g = e / rows, r = e - g * rows;
-                if (e < G * rows)
-                    *reinterpret_cast<uint4*>(sX + g * plane + r * 16) =
-                        make_uint4(w4[u][0], w4[u][1], w4[u][2], w4[u][3]);
-            }
+            for (int u = 0; u < TC_BATCH; ++u)
+                if (dst[u] >= 0)
+                    *reinterpret_cast<uint4*>(sX + dst[u]) = make_uint4(w4[u][0], w4[u][1], w4[u][2], w4[u][3]);
         }
         // the tile written by this CTA's threads becomes visible to the tensor cores
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -294,107 +283,335 @@ __global__ void __launch_bounds__(TC_PIX) conv3x3_tc_kernel(const bf16* __restri
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(taddr) : "memory");
 }
 
-// Weight gradient partials: part[s][m][n] = sum over pixels q in split s of
-// dy[b][m][p] * patch(x)[n][b, p], n < N = C*9 (padded to Np = 288 columns).
-__global__ void __launch_bounds__(CONV_THREADS) conv3x3_wgrad_kernel(const bf16* __restrict__ dy, int M,
-                                                                     const bf16* __restrict__ x, int B, int C,
-                                                                     int H, int W, float* __restrict__ part) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int N = C * 9;
-    const long long HW = (long long)H * W, P = (long long)B * HW;
-    const long long q0 = (long long)blockIdx.x * WG_SPLIT;
-    const long long q1 = q0 + WG_SPLIT < P ? q0 + WG_SPLIT : P;
-    float acc[2][WG_NT][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int j = 0; j < WG_NT; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[mt][j][e] = 0.f;
+// ------------------------------------------------------------------ tcgen05 weight gradient
+//
+// dW[m][c][di][dj] = sum_{b, pixel} dy[b][m][pixel] x[b][c][pixel + (di - 1, dj - 1)]
+// is a GEMM whose contraction runs over pixels: D[(t, c)][m] = sum_pos
+// P[(t, c)][pos] dy[m][pos] with P the patch matrix (t = 3 di + dj), M = 9 Cp
+// rows (Cp = 16 ceil(C / 16)) in blocks of 128, N = 32, K = the 128 virtual
+// positions of a tile (the forward kernel's layout, halo columns and rows past
+// the image carrying dy = 0).  A tap is a shift along K here, which no
+// descriptor start address can express at element granularity, so each tile
+// builds P explicitly in shared memory: the input tile is staged
+// position-contiguous per channel (sX[c][r], r = 0 .. XR - 1 from virtual
+// position v0 - Wv - 1; XR = 2 mod 4 so that a warp's 32 channels hit 32
+// banks), and each 16-byte row piece of P, x[c][r + shift_t .. + 7], is put
+// together from five aligned words (a byte permute when the shift is odd).
+// P is K-major: core matrix (rows 8g.., positions 8k..) at 128 (k 9Cp/8 + g);
+// dy is staged K-major too: core matrix (channels 8a.., positions 8k..) at
+// 128 (4k + a).  The three (two for C <= 16) M-blocks accumulate in 32
+// tensor-memory columns each across all the tiles a CTA takes; the rows of
+// the last block past 9 Cp read whatever follows P in shared memory (the
+// staged input) and are never read back.  Each CTA writes its partial
+// part[cta][m][9c + t]; wgrad_reduce_kernel sums them in CTA order.  Staging
+// the next tile's input and dy overlaps the previous tile's MMAs.
+constexpr int WG_THREADS = 256;
+constexpr int WG_TILE = 128;   // positions per tile (the K of one tile's MMAs)
+constexpr int WG_BATCH = 8;    // input pairs a thread loads before storing them
 
-    for (long long qk = q0; qk < q1; qk += 16) {
-        // pixels of this k-step handled by the thread: qk + 2t + {0, 1, 8, 9}
-        long long qs[4] = {qk + 2 * t, qk + 2 * t + 1, qk + 2 * t + 8, qk + 2 * t + 9};
-        int bq[4], iq[4], jq[4];
-        bool ok[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            ok[e] = qs[e] < q1;
-            const long long qq = ok[e] ? qs[e] : q0;
-            bq[e] = (int)(qq / HW);
-            const long long r = qq - (long long)bq[e] * HW;
-            iq[e] = (int)(r / W);
-            jq[e] = (int)(r - (long long)iq[e] * W);
-        }
-        // A fragment from dy: rows m = mt*16 + g (+8), columns k = pixels
-        uint32_t a[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            bf16 v[8];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = mt * 16 + g + 8 * h;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const long long p = (long long)iq[e] * W + jq[e];
-                    v[h * 4 + e] = (m < M && ok[e]) ? dy[((long long)bq[e] * M + m) * HW + p] : __float2bfloat16_rn(0.f);
-                }
-            }
-            // v[h*4 + e]: h = row half (g / g+8), e = pixel slot (2t, 2t+1, 2t+8, 2t+9)
-            a[mt][0] = pack2(v[0], v[1]);
-            a[mt][1] = pack2(v[4], v[5]);
-            a[mt][2] = pack2(v[2], v[3]);
-            a[mt][3] = pack2(v[6], v[7]);
-        }
-#pragma unroll
-        for (int j = 0; j < WG_NT; ++j) {
-            const int n = (warp + 4 * j) * 8 + g;  // this thread's B column
-            uint32_t b0 = pack2(patch(x, n, N, bq[0], iq[0], jq[0], C, H, W, ok[0]),
-                                patch(x, n, N, bq[1], iq[1], jq[1], C, H, W, ok[1]));
-            uint32_t b1 = pack2(patch(x, n, N, bq[2], iq[2], jq[2], C, H, W, ok[2]),
-                                patch(x, n, N, bq[3], iq[3], jq[3], C, H, W, ok[3]));
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][j], a[mt], b0, b1);
-        }
-    }
-    float* out = part + (long long)blockIdx.x * MAX_ROWS * 288;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int j = 0; j < WG_NT; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int m = mt * 16 + g + (e >= 2 ? 8 : 0);
-                const int n = (warp + 4 * j) * 8 + 2 * t + (e & 1);
-                out[m * 288 + n] = acc[mt][j][e];
-            }
+__host__ __device__ inline int wg_xrows(int Wv) {
+    const int r = WG_TILE + 2 * Wv + 4;  // shifts up to 2 Wv + 2, plus one word read ahead
+    return r + ((2 - (r & 3)) & 3);
+}
+// patch matrix, input tile, dy tile, position tables (input rows and the
+// tile's outputs, ints), mbarrier + tensor-memory address slot
+__host__ __device__ inline size_t wg_smem_bytes(int C, int Wv) {
+    const int Cp = 16 * ((C + 15) / 16);
+    return (size_t)9 * Cp * WG_TILE * 2 + (size_t)Cp * wg_xrows(Wv) * 2 + (size_t)32 * WG_TILE * 2 +
+           (size_t)(wg_xrows(Wv) + 2 + WG_TILE) * 4 + 16;
 }
 
-// dw[m][n] = sum_s part[s][m][n] in split order (deterministic), n < C*9.
-__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int S, int M, int N, float* __restrict__ dw) {
+__device__ __forceinline__ bool wg_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done = 0;
+    unsigned long long t0, t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!done) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(tc_smem(bar)), "r"(parity)
+            : "memory");
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        if (!done && t1 - t0 > TC_WAIT_NS) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(WG_THREADS) conv3x3_wgrad_tc_kernel(const bf16* __restrict__ dy, int M,
+                                                                      const bf16* __restrict__ x, int C, int H,
+                                                                      int W, TcGeom geo, float* __restrict__ part) {
+    extern __shared__ __align__(1024) uint8_t wg_sm[];
+    const int Cp = 16 * ((C + 15) / 16), R9 = 9 * Cp, RG = R9 / 8, nblk = (R9 + 127) / 128;
+    const int Wt = geo.Wt, Wv = geo.Wv, XR = wg_xrows(Wv);
+    uint8_t* sA = wg_sm;                                   // patch matrix, R9 x 128 positions
+    uint16_t* sX = reinterpret_cast<uint16_t*>(wg_sm + (size_t)R9 * WG_TILE * 2);  // Cp x XR
+    uint8_t* sB = reinterpret_cast<uint8_t*>(sX + (size_t)Cp * XR);               // 32 x 128 dy
+    int* xoff = reinterpret_cast<int*>(sB + 32 * WG_TILE * 2);  // image offset of input row r, -1 outside
+    int* yoff = xoff + XR + 2;                                  // image offset of output position r, -1 if none
+    uint64_t* bar = reinterpret_cast<uint64_t*>(yoff + WG_TILE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long HW = (long long)H * W;
+    // first pair (c, pair) of the input staging, first patch piece (kc, R),
+    // and the steps between a thread's items
+    const int HP = XR / 2;
+    const int c0 = tid / HP, rp0 = tid - c0 * HP, dc = WG_THREADS / HP, drp = WG_THREADS - dc * HP;
+    const int kc0 = tid / R9, R0 = tid - kc0 * R9, dk = WG_THREADS / R9, dR = WG_THREADS - dk * R9;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc_smem(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = *tslot;
+    const uint32_t idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+    bool ok = true;
+    uint32_t it = 0;
+    for (long long tile = blockIdx.x; tile < geo.tiles; tile += gridDim.x, ++it) {
+        const long long bs = tile / geo.tps;
+        const int k = (int)(tile - bs * geo.tps);
+        const int b = (int)(bs / geo.strips), s = (int)(bs - (long long)b * geo.strips);
+        const int v0 = Wv + k * WG_TILE, vlo = v0 - Wv - 1;
+        const bf16* xb = x + (long long)b * C * HW;
+        const bf16* db = dy + (long long)b * M * HW;
+        // position tables (their previous readers finished before the barrier
+        // ahead of the previous tile's MMAs)
+        for (int r = tid; r < XR + WG_TILE; r += WG_THREADS) {
+            if (r < XR) {
+                xoff[r] = tc_offset(vlo + r, s, Wt, Wv, H, W);
+            } else {
+                const int v = v0 + (r - XR);
+                const int i = v / Wv - 1, jj = v - (i + 1) * Wv - 1;
+                yoff[r - XR] = (jj >= 0 && jj < Wt) ? tc_offset(v, s, Wt, Wv, H, W) : -1;
+            }
+        }
+        __syncthreads();
+        // input tile -> sX (pairs of positions); sX is free: the previous
+        // tile's patch matrix was built before its MMAs were issued
+        // (WG_BATCH pairs per thread in flight before their stores)
+        const int npair = Cp * HP;
+        int c = c0, rp = rp0;
+        for (int e0 = 0; e0 < npair; e0 += WG_BATCH * WG_THREADS) {
+            uint32_t h2[WG_BATCH];
+            int dst[WG_BATCH];
+#pragma unroll
+            for (int u = 0; u < WG_BATCH; ++u) {
+                const bool in = e0 + u * WG_THREADS + tid < npair;
+                dst[u] = in ? c * HP + rp : -1;
+                h2[u] = 0u;
+                if (in && c < C) {
+                    const int oa = xoff[2 * rp], ob = xoff[2 * rp + 1];
+                    const bf16* xc = xb + (long long)c * HW;
+                    if (oa >= 0) h2[u] = __bfloat16_as_ushort(xc[oa]);
+                    if (ob >= 0) h2[u] |= (uint32_t)__bfloat16_as_ushort(xc[ob]) << 16;
+                }
+                rp += drp;
+                c += dc;
+                if (rp >= HP) {
+                    rp -= HP;
+                    ++c;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < WG_BATCH; ++u)
+                if (dst[u] >= 0) reinterpret_cast<uint32_t*>(sX)[dst[u]] = h2[u];
+        }
+        // dy pieces (channel m, positions 8kc .. 8kc + 7) into registers
+        uint4 dpc[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int p = tid + u * WG_THREADS, kc = p & 15, m = p >> 4;
+            uint32_t w4[4] = {0u, 0u, 0u, 0u};
+            if (m < M) {
+                const bf16* dm = db + (long long)m * HW;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int o = yoff[8 * kc + e];
+                    if (o >= 0) w4[e >> 1] |= (uint32_t)__bfloat16_as_ushort(dm[o]) << (16 * (e & 1));
+                }
+            }
+            dpc[u] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        // the previous tile's MMAs must be done before sA and sB are rewritten
+        if (it > 0) ok = wg_wait(bar, (it - 1) & 1u);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int p = tid + u * WG_THREADS, kc = p & 15, m = p >> 4;
+            *reinterpret_cast<uint4*>(sB + (kc * 4 + (m >> 3)) * 128 + (m & 7) * 16) = dpc[u];
+        }
+        // patch matrix: piece (row R = t Cp + c, position chunk kc)
+        const uint32_t* sX32 = reinterpret_cast<const uint32_t*>(sX);
+        int kc = kc0, R = R0;
+        for (int p = tid; p < R9 * (WG_TILE / 8); p += WG_THREADS) {
+            const int t = R / Cp, c = R - t * Cp;
+            const int e0 = c * XR + (t / 3) * Wv + (t % 3) + 8 * kc;
+            const uint32_t* w = sX32 + (e0 >> 1);
+            const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
+            uint4 v;
+            if (e0 & 1) {
+                const uint32_t w4 = w[4];
+                v = make_uint4(__byte_perm(w0, w1, 0x5432), __byte_perm(w1, w2, 0x5432), __byte_perm(w2, w3, 0x5432),
+                               __byte_perm(w3, w4, 0x5432));
+            } else {
+                v = make_uint4(w0, w1, w2, w3);
+            }
+            *reinterpret_cast<uint4*>(sA + (kc * RG + (R >> 3)) * 128 + (R & 7) * 16) = v;
+            R += dR;
+            kc += dk;
+            if (R >= R9) {
+                R -= R9;
+                ++kc;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t a0 = tc_smem(sA), b0 = tc_smem(sB);
+            for (int blk = 0; blk < nblk; ++blk)
+                for (int kk = 0; kk < WG_TILE / 16; ++kk) {
+                    const uint64_t ad = tc_desc(a0 + (2 * kk * RG + 16 * blk) * 128, RG * 128, 128);
+                    const uint64_t bd = tc_desc(b0 + kk * 1024, 512, 128);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr + 32 * blk),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"((uint32_t)(it > 0 || kk > 0))
+                        : "memory");
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tc_smem(bar))
+                         : "memory");
+        }
+    }
+    if (ok && it > 0) ok = wg_wait(bar, (it - 1) & 1u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = !__syncthreads_or(!ok);
+    // partial: warp w reads tensor-memory lanes 32 (w % 4) .. of blocks w / 4, w / 4 + 2
+    float* out = part + (long long)blockIdx.x * MAX_ROWS * 288;
+    const int q = warp & 3;
+    for (int blk = warp >> 2; blk < nblk; blk += 2) {
+        uint32_t r[32];
+        if (ok) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                "[%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr + ((uint32_t)(32 * q) << 16) + 32 * blk));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+            for (int m = 0; m < 32; ++m) r[m] = 0x7fc00000u;  // NaN: a CTA that gave up poisons dW
+        }
+        const int R = blk * 128 + 32 * q + lane;
+        if (R < R9) {
+            const int t = R / Cp, c = R - t * Cp;
+            if (c < C) {
+#pragma unroll
+                for (int m = 0; m < 32; ++m)
+                    if (m < M) out[m * 288 + 9 * c + t] = __uint_as_float(r[m]);
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicAdd(&g_conv_timeouts, 1ull);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(taddr) : "memory");
+}
+
+// dw[m][n] = sum_s part[s][m][n] in split order (deterministic), n < C*9; the
+// loads run 8 partials ahead of the (sequential) sum.
+__global__ void __launch_bounds__(64) wgrad_reduce_kernel(const float* __restrict__ part, int S, int M, int N,
+                                                          float* __restrict__ dw) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * N) return;
     const int m = idx / N, n = idx - m * N;
+    const float* p = part + m * 288 + n;
     float s = 0.f;
-    for (int k = 0; k < S; ++k) s += part[(long long)k * MAX_ROWS * 288 + m * 288 + n];
+    int k = 0;
+    for (; k + 8 <= S; k += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = p[(long long)(k + u) * MAX_ROWS * 288];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; k < S; ++k) s += p[(long long)k * MAX_ROWS * 288];
     dw[idx] = s;
 }
 
-// db[m] = sum over (b, p) of dy32[b][m][p]; one block per m, fixed tree.
-__global__ void bias_grad_kernel(const float* __restrict__ dy, int B, int M, long long HW, float* __restrict__ db) {
+// db[m] = sum over (b, p) of dy32[b][m][p], in two fixed-order levels: block
+// (sp, m) sums the sp-th of DB_SPLIT equal ranges of the flattened (b, p)
+// index (each thread a strided subsequence, then a fixed tree) into
+// partial[m][sp]; bias_grad_sum_kernel adds the DB_SPLIT partials in order.
+constexpr int DB_SPLIT = 64;
+__global__ void __launch_bounds__(256) bias_grad_kernel(const float* __restrict__ dy, int B, int M, long long HW,
+                                                        float* __restrict__ partial) {
     __shared__ float sm[256];
-    const int m = blockIdx.x;
+    const int sp = blockIdx.x, m = blockIdx.y;
+    const long long n = (long long)B * HW, L = (n + DB_SPLIT - 1) / DB_SPLIT;
+    const long long q0 = sp * L, q1 = q0 + L < n ? q0 + L : n;
     float s = 0.f;
-    for (int b = 0; b < B; ++b)
-        for (long long p = threadIdx.x; p < HW; p += 256) s += dy[((long long)b * M + m) * HW + p];
+    long long q = q0 + threadIdx.x;
+    long long b = q / HW, p = q - b * HW;
+    for (; q + 768 < q1; q += 1024) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            v[u] = dy[(b * M + m) * HW + p];
+            p += 256;
+            while (p >= HW) {
+                p -= HW;
+                ++b;
+            }
+        }
+        s += v[0];
+        s += v[1];
+        s += v[2];
+        s += v[3];
+    }
+    for (; q < q1; q += 256) {
+        s += dy[(b * M + m) * HW + p];
+        p += 256;
+        while (p >= HW) {
+            p -= HW;
+            ++b;
+        }
+    }
     sm[threadIdx.x] = s;
     __syncthreads();
     for (int k = 128; k > 0; k >>= 1) {
         if ((int)threadIdx.x < k) sm[threadIdx.x] += sm[threadIdx.x + k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) db[m] = sm[0];
+    if (threadIdx.x == 0) partial[m * DB_SPLIT + sp] = sm[0];
+}
+
+__global__ void bias_grad_sum_kernel(const float* __restrict__ partial, int M, float* __restrict__ db) {
+    const int m = threadIdx.x;
+    if (m >= M) return;
+    float s = 0.f;
+    for (int k = 0; k < DB_SPLIT; ++k) s += partial[m * DB_SPLIT + k];
+    db[m] = s;
 }
 
 // Element idx of the tensor-core weight operand (tile order of
@@ -517,34 +734,53 @@ int status_of(cudaError_t e) { return e == cudaSuccess ? TLBM_OK : TLBM_ERR_CUDA
 
 bool conv_shape_ok(int B, int C, int M, int H, int W) {
     return B > 0 && C > 0 && C <= 32 && M > 0 && M <= MAX_ROWS && H > 0 && W > 0 &&
-           (long long)B * H * W < (1ll << 40) && (long long)H * TC_PIX < (1ll << 30);
+           (long long)B * H * W < (1ll << 40) && (long long)H * W < (1ll << 31) && (long long)H * TC_PIX < (1ll << 30);
 }
 
 // Persistent launch: as many CTAs as fit the SMs at once (about 43 KB of
 // shared memory each at 32 channels), never more than there are tiles.
-int launch_tc(const bf16* A, int M, const bf16* x, int B, int C, int H, int W, const float* bias, int relu,
-              float* out, bf16* out_act, cudaStream_t s) {
+// Tiles of 128 virtual positions (both tensor-core kernels walk the same layout).
+TcGeom tc_geometry(int B, int H, int W) {
     TcGeom geo;
     geo.Wt = W < TC_WT ? W : TC_WT;
     geo.Wv = geo.Wt + 2;
     geo.strips = (W + geo.Wt - 1) / geo.Wt;
     geo.tps = (int)(((long long)H * geo.Wv + TC_PIX - 1) / TC_PIX);
     geo.tiles = (long long)B * geo.strips * geo.tps;
-    const size_t smem = tc_smem_bytes(C, geo.Wv);
-    // CTAs resident per SM: as many as shared memory holds (228 KB per SM,
-    // 1 KB reserved per CTA), at most 8 (each holds 32 of the SM's 512
-    // tensor-memory columns); launched with the largest shared-memory carveout.
-    static const cudaError_t carve = cudaFuncSetAttribute(
-        conv3x3_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    return geo;
+}
+
+// Persistent grid: CTAs resident per SM as many as shared memory holds (228 KB
+// per SM, 1 KB reserved per CTA), at most `cap` (tensor-memory columns: an SM
+// has 512), never more CTAs than tiles.
+int persistent_grid(long long tiles, size_t smem, long long cap, long long* grid) {
     int dev = 0, sms = 0;
-    if (carve != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+    if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return TLBM_ERR_CUDA;
     long long per = (long long)(228 * 1024) / (long long)(smem + 1024);
-    per = per < 1 ? 1 : (per > 8 ? 8 : per);
-    const long long grid = geo.tiles < sms * per ? geo.tiles : sms * per;
+    per = per < 1 ? 1 : (per > cap ? cap : per);
+    *grid = tiles < sms * per ? tiles : sms * per;
+    return TLBM_OK;
+}
+
+int launch_tc(const bf16* A, int M, const bf16* x, int B, int C, int H, int W, const float* bias, int relu,
+              float* out, bf16* out_act, cudaStream_t s) {
+    const TcGeom geo = tc_geometry(B, H, W);
+    const size_t smem = tc_smem_bytes(C, geo.Wv);
+    // launched with the largest shared-memory carveout so that the CTAs counted fit
+    static const cudaError_t carve = cudaFuncSetAttribute(
+        conv3x3_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    long long grid = 0;
+    if (carve != cudaSuccess || persistent_grid(geo.tiles, smem, 8, &grid) != TLBM_OK) return TLBM_ERR_CUDA;
     conv3x3_tc_kernel<<<(unsigned)grid, TC_PIX, smem, s>>>(A, M, x, C, H, W, bias, relu, out, out_act, geo);
     return status_of(cudaGetLastError());
+}
+
+// Weight-gradient grid (the number of partials) for a shape.
+int wgrad_grid(int B, int C, int H, int W, long long* grid) {
+    const TcGeom geo = tc_geometry(B, H, W);
+    return persistent_grid(geo.tiles, wg_smem_bytes(C, geo.Wv), 4, grid);
 }
 
 }  // namespace
@@ -584,9 +820,9 @@ extern "C" int tlbm_conv3x3_status(unsigned long long* timeouts) {
 
 extern "C" int tlbm_conv3x3_workspace_bytes(int B, int cin, int cout, int H, int W, size_t* bytes) {
     if (!bytes || !conv_shape_ok(B, cin, cout, H, W)) return TLBM_ERR_ARG;
-    const long long P = (long long)B * H * W;
-    const long long S = (P + WG_SPLIT - 1) / WG_SPLIT;
-    const size_t part = (size_t)S * MAX_ROWS * 288 * sizeof(float);
+    long long S = 0;
+    if (wgrad_grid(B, cin, H, W, &S) != TLBM_OK) return TLBM_ERR_CUDA;
+    const size_t part = ((size_t)S * MAX_ROWS * 288 + (size_t)MAX_ROWS * DB_SPLIT) * sizeof(float);
     const size_t at = (size_t)MAX_ROWS * 288 * sizeof(bf16);
     *bytes = part > at ? part : at;
     return TLBM_OK;
@@ -599,19 +835,29 @@ extern "C" int tlbm_conv3x3_backward_weight(const void* x, const void* dy_bf16, 
     size_t need = 0;
     tlbm_conv3x3_workspace_bytes(B, cin, cout, H, W, &need);
     if (workspace_bytes < need) return TLBM_ERR_OOM;
-    const long long P = (long long)B * H * W;
-    const int S = (int)((P + WG_SPLIT - 1) / WG_SPLIT);
+    const TcGeom geo = tc_geometry(B, H, W);
+    const size_t smem = wg_smem_bytes(cin, geo.Wv);
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        conv3x3_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wg_smem_bytes(32, TC_PIX));
+    static const cudaError_t carve = cudaFuncSetAttribute(
+        conv3x3_wgrad_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    long long S = 0;
+    if (attr != cudaSuccess || carve != cudaSuccess || wgrad_grid(B, cin, H, W, &S) != TLBM_OK) return TLBM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    conv3x3_wgrad_kernel<<<S, CONV_THREADS, 0, s>>>((const bf16*)dy_bf16, cout, (const bf16*)x, B, cin, H, W,
-                                                    (float*)workspace);
+    conv3x3_wgrad_tc_kernel<<<(unsigned)S, WG_THREADS, smem, s>>>((const bf16*)dy_bf16, cout, (const bf16*)x, cin, H,
+                                                                  W, geo, (float*)workspace);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return TLBM_ERR_CUDA;
-    wgrad_reduce_kernel<<<grid_for((long long)cout * cin * 9, 256), 256, 0, s>>>((const float*)workspace, S, cout,
-                                                                               cin * 9, dw);
+    wgrad_reduce_kernel<<<grid_for((long long)cout * cin * 9, 64), 64, 0, s>>>((const float*)workspace, (int)S,
+                                                                             cout, cin * 9, dw);
     e = cudaGetLastError();
     if (e != cudaSuccess) return TLBM_ERR_CUDA;
     if (db && dy) {
-        bias_grad_kernel<<<cout, 256, 0, s>>>(dy, B, cout, (long long)H * W, db);
+        float* partial = (float*)workspace + (size_t)S * MAX_ROWS * 288;
+        bias_grad_kernel<<<dim3(DB_SPLIT, cout), 256, 0, s>>>(dy, B, cout, (long long)H * W, partial);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return TLBM_ERR_CUDA;
+        bias_grad_sum_kernel<<<1, MAX_ROWS, 0, s>>>(partial, cout, db);
         e = cudaGetLastError();
     }
     return status_of(e);
