@@ -335,7 +335,7 @@ def run_batch(prec: str, steps: int, warmup: int, ws: int, device_index: int) ->
         ev1.synchronize()
         sec = ev0.elapsed_time(ev1) / 1e3
         out["batched"] = {"sec": max_over_ranks(sec, ws, torch.device("cuda", device_index) if ws > 1 else None),
-                          "launches": b.launches - l0, "variant": list(b.variant),
+                          "launches": b.launches - l0, "variant": list(b.variant), "staged": b.staged[0],
                           "diverged": sum(b.status())}
         # the persistent form: 64 steps per cooperative launch, grid barrier between steps
         b.set_persistent(64)
@@ -560,6 +560,7 @@ def main():
                 "persistent": round(r["nodes"] * ws * st / r["persistent"]["sec"] / 1e9, 3),
                 "separate": round(r["nodes"] * ws * st / sp["sec"] / 1e9, 3),
                 "speedup": round(sp["sec"] / bt["sec"], 3), "diverged": bt["diverged"],
+                "form": f"staged{bt['staged']}" if bt["staged"] else f"vec{bt['variant'][0]}",
             }
             continue
         st = args.steps if not v.endswith("fp64") else max(10, args.steps // 10)

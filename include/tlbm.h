@@ -314,11 +314,12 @@ TLBM_API int tlbm_batch_set_variant(tlbm_batch_t b, int vec, int form, int block
  * that waits too long gives up, and tlbm_batch_status then returns
  * TLBM_ERR_TIMEOUT.  TLBM_ERR_UNSUPPORTED without cooperative launch. */
 TLBM_API int tlbm_batch_set_persistent(tlbm_batch_t b, int steps_per_launch);
-/* How long a block of the persistent kernel waits at the grid barrier before it
- * gives up (default 0.5 s; 0 gives up at once unless the barrier is already
- * open, which makes the timeout path testable).  seconds in [0, 10], else
- * TLBM_ERR_ARG.  The timeout stays reported by tlbm_batch_status until
- * tlbm_batch_init. */
+/* How long a block of the persistent kernel waits at the grid barrier, and a
+ * block of the staged form for its copies or a free stage, before it gives up
+ * (default 0.5 s; 0 gives up at once unless the barrier is already open or the
+ * copies have landed, which makes the timeout path testable).  seconds in
+ * [0, 10], else TLBM_ERR_ARG.  The timeout stays reported by tlbm_batch_status
+ * until tlbm_batch_init. */
 TLBM_API int tlbm_batch_set_wait_limit(tlbm_batch_t b, double seconds);
 TLBM_API int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* block_x, int* block_y,
                                     int* graph_steps);
@@ -330,9 +331,23 @@ TLBM_API int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* bl
  * tlbm_batch_autotune tries both. */
 TLBM_API int tlbm_batch_set_rows(tlbm_batch_t b, int rows);
 TLBM_API int tlbm_batch_get_rows(tlbm_batch_t b, int* rows);
+/* Shared-memory staged form of the flattened launch (the single-cell staged
+ * kernel's pipeline, tlbm_set_staged, over the tiles of every instance):
+ * consumer_warps 4 or 8 in 2D, 4 or 7 in 3D (tiles of up to 64 x that many
+ * nodes; each instance's rows are cut into the fewest equal segments), 0 turns
+ * it off; stages 0 chooses the tiles in flight per block, else 2 .. 8.  FP32,
+ * FP16 or BF16 storage with two-relaxation-time rates in every instance
+ * (TLBM_ERR_UNSUPPORTED otherwise, and for the persistent form).
+ * tlbm_batch_set_variant turns it off; tlbm_batch_autotune times it against
+ * the register-kernel shapes.  A block that waits longer than the wait limit
+ * for its copies gives up; tlbm_batch_status then returns TLBM_ERR_TIMEOUT. */
+TLBM_API int tlbm_batch_set_staged(tlbm_batch_t b, int consumer_warps, int stages);
+/* The staged form's consumer warps (0: off), stages and tiles per step. */
+TLBM_API int tlbm_batch_get_staged(tlbm_batch_t b, int* consumer_warps, int* stages, long long* tiles);
 /* Time the compiled launch shapes (nodes per thread x rows per thread x block
- * shape, trials launches each) on the bound state and keep the fastest.  The
- * state is not changed. */
+ * shape, then tiles per block, then the staged form where it applies; trials
+ * launches each) on the bound state and keep the fastest.  The state is not
+ * changed. */
 TLBM_API int tlbm_batch_autotune(tlbm_batch_t b, int trials);
 /* (trials < 0: reuse the shape this process tuned for the same lattice, storage,
  * collision form and size class floor(log2(total nodes)), if any.) */

@@ -34,6 +34,7 @@ UNITS = {
     "noalloc.cu": [],
     "step_staged.cu": [],
     "batch.cu": [],
+    "batch_staged.cu": [],
     "conv.cu": [],
     "peak.cu": [],
 }

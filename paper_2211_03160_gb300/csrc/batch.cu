@@ -19,18 +19,13 @@
 #include <vector>
 
 #include "../../include/tlbm.h"
+#include "batch.h"
 #include "dispatch.h"
 #include "handle.h"
 
 using namespace tlbm;
 
 namespace {
-
-struct BatchInst {
-    const void* buf[2];  // population buffers of the instance
-    long long block0;    // first flattened block of the instance
-    int gx, gy;          // blocks along x and y of the instance (z: nz)
-};
 
 // Tile b of the flattened grid belongs to the instance i with
 // block0[i] <= b < block0[i+1]; its parameters are staged in shared memory.
@@ -130,8 +125,8 @@ __global__ void batch_step_kernel(const KParams* __restrict__ kps, const BatchIn
 struct GridSync {
     unsigned count;
     unsigned gen;
-    int status;  // 1: a block gave up waiting (TLBM_ERR_TIMEOUT)
-    int pad;
+    int status;         // 1: a block gave up waiting (TLBM_ERR_TIMEOUT)
+    int staged_status;  // 1: a block of the staged form gave up waiting for its copies
 };
 constexpr unsigned long long GRID_WAIT_NS = 500000000;  // default: 0.5 s
 
@@ -297,6 +292,11 @@ struct tlbm_batch_s {
     int tpb;            // tiles per block of the flattened launch
     int graph_steps;
     int persist_steps;  // > 0: persistent kernel, this many steps per launch
+    int staged_nc;      // > 0: shared-memory staged form with this many consumer warps
+    int staged_stages;
+    long long staged_cap;  // co-resident blocks of the staged kernel (blocks per SM x SMs)
+    size_t staged_smem;
+    long long staged_tiles;
     unsigned long long wait_ns;  // grid-barrier wait limit of the persistent kernel
     long long total_blocks;
     int parity;
@@ -354,7 +354,7 @@ static int eff_rows(tlbm_batch_t b) { return b->persist_steps > 0 ? 1 : b->rows;
 static void build_tables(tlbm_batch_t b, std::vector<KParams>& kps, std::vector<BatchInst>& ins) {
     kps.resize(b->n);
     ins.resize(b->n);
-    long long block0 = 0;
+    long long block0 = 0, stile0 = 0;
     for (int i = 0; i < b->n; ++i) {
         tlbm_t h = b->inst[i];
         kps[i] = h->kp;
@@ -369,8 +369,21 @@ static void build_tables(tlbm_batch_t b, std::vector<KParams>& kps, std::vector<
         ins[i].gx = gx;
         ins[i].gy = gy;
         block0 += (long long)gx * gy * h->nz;
+        // staged form: rows cut into the fewest segments of at most 64 NC nodes,
+        // of equal width rounded up to the 16-byte copy granule
+        ins[i].stile0 = stile0;
+        ins[i].stw = ins[i].stpr = 0;
+        if (b->staged_nc > 0) {
+            const int twmax = 64 * b->staged_nc, A = 16 / (int)h->elem;
+            const int segs = (h->nx + twmax - 1) / twmax;
+            const int tw = ((h->nx + segs - 1) / segs + A - 1) / A * A;
+            ins[i].stw = tw;
+            ins[i].stpr = (h->nx + tw - 1) / tw;
+            stile0 += (long long)h->ny * h->nz * ins[i].stpr;
+        }
     }
     b->total_blocks = block0;
+    b->staged_tiles = stile0;
 }
 
 static int upload_tables(tlbm_batch_t b) {
@@ -387,6 +400,12 @@ static int upload_tables(tlbm_batch_t b) {
 }
 
 static cudaError_t launch_batch(tlbm_batch_t b, int parity, cudaStream_t s) {
+    if (b->staged_nc > 0) {
+        BatchStagedInfo si{b->staged_tiles, b->staged_stages, &b->d_sync->staged_status, b->wait_ns};
+        const int grid = (int)std::min<long long>(b->staged_tiles, b->staged_cap);
+        return launch_batch_staged(b->dim, b->prec, b->staged_nc, b->d_kp, b->d_inst, b->n, parity, si, grid,
+                                   b->staged_smem, s);
+    }
     return batch_dispatch(true, b->dim, b->prec, b->vec, b->trt != 0, b->d_kp, b->d_inst, b->n, parity,
                           b->total_blocks, dim3(b->bx, b->by, 1), s, nullptr, eff_rows(b), b->tpb);
 }
@@ -593,6 +612,7 @@ extern "C" int tlbm_batch_set_variant(tlbm_batch_t b, int vec, int form, int blo
     b->bx = bx;
     b->by = by;
     b->graph_steps = graph_steps;
+    b->staged_nc = 0;  // an explicit register-kernel shape
     if (batch_dispatch(false, b->dim, b->prec, v, trt != 0, nullptr, nullptr, 0, 0, 0, dim3(), nullptr, nullptr, b->rows) !=
         cudaSuccess)
         b->rows = 1;  // no pipelined-row variant for this one
@@ -632,6 +652,92 @@ extern "C" int tlbm_batch_get_rows(tlbm_batch_t b, int* rows) {
     return TLBM_OK;
 }
 
+// The staged form needs 16-bit or FP32 storage and two-relaxation-time rates
+// in every instance (and is not the persistent form).
+static bool staged_possible(tlbm_batch_t b) {
+    if (b->prec == TLBM_FP64 || b->persist_steps > 0) return false;
+    for (tlbm_t h : b->inst)
+        if (!h->kp.trt) return false;
+    return true;
+}
+
+// Staged form with nc consumer warps (0: off) and `stages` tiles in flight per
+// block (0: the most tiles in flight per SM up to six, more blocks first, as
+// for a single cell).
+static int batch_set_staged(tlbm_batch_t b, int nc, int stages) {
+    if (nc == 0) {
+        b->staged_nc = 0;
+        return b->mem ? upload_tables(b) : TLBM_OK;
+    }
+    if (b->prec == TLBM_FP64) return bfail(b, TLBM_ERR_UNSUPPORTED, "the staged form has no FP64 variant");
+    for (tlbm_t h : b->inst)
+        if (!h->kp.trt) return bfail(b, TLBM_ERR_UNSUPPORTED, "the staged form needs two-relaxation-time rates");
+    const int big = b->dim == 3 ? 7 : 8;
+    if (nc != 4 && nc != big) return bfail(b, TLBM_ERR_ARG, "consumer warps must be 4 or %d", big);
+    if (stages != 0 && (stages < 2 || stages > TILE_MAX_STAGES))
+        return bfail(b, TLBM_ERR_ARG, "stages must be 0 or in [2, %d]", TILE_MAX_STAGES);
+    const void* fn = batch_staged_function(b->dim, b->prec, nc);
+    if (!fn) return bfail(b, TLBM_ERR_UNSUPPORTED, "staged batch kernel not built for this storage");
+    const tlbm_t h0 = b->inst[0];
+    const int A = 16 / (int)h0->elem;
+    const size_t stage_bytes = (size_t)(h0->qf + h0->qg) * (64 * nc + 2 * A) * h0->elem;
+    int dev = 0, optin = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "staged form setup: %s", cudaGetErrorString(e));
+    const int threads = 32 * (nc + 1);
+    int ns = stages;
+    if (ns == 0) {
+        int first = 0, best_in = 0, best_b = 0;
+        for (int k = 2; k <= TILE_MAX_STAGES; ++k) {
+            int blocks = 0;
+            const size_t sm = 512 + (size_t)k * stage_bytes;
+            if (sm > (size_t)optin) break;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, sm);
+            if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+            if (blocks < 1) break;
+            if (!first) first = k;
+            const int in = blocks * k;
+            if (in <= 6 && (in > best_in || (in == best_in && blocks > best_b))) {
+                ns = k;
+                best_in = in;
+                best_b = blocks;
+            }
+        }
+        if (ns == 0) ns = first;
+        if (ns == 0) return bfail(b, TLBM_ERR_ARG, "two stages of %zu bytes do not fit in shared memory", stage_bytes);
+    }
+    const size_t smem = 512 + (size_t)ns * stage_bytes;
+    if (smem > (size_t)optin) return bfail(b, TLBM_ERR_ARG, "%zu bytes of shared memory per block exceed %d", smem, optin);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (e != cudaSuccess || per_sm < 1)
+        return bfail(b, TLBM_ERR_ARG, "%zu bytes of shared memory per block do not fit", smem);
+    b->staged_nc = nc;
+    b->staged_stages = ns;
+    b->staged_smem = smem;
+    b->staged_cap = (long long)per_sm * sms;
+    if (b->mem) return upload_tables(b);
+    return TLBM_OK;
+}
+
+extern "C" int tlbm_batch_set_staged(tlbm_batch_t b, int consumer_warps, int stages) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (consumer_warps != 0 && b->persist_steps > 0)
+        return bfail(b, TLBM_ERR_UNSUPPORTED, "the persistent form has no staged variant");
+    if (consumer_warps < 0) return bfail(b, TLBM_ERR_ARG, "consumer_warps must be >= 0");
+    return batch_set_staged(b, consumer_warps, stages);
+}
+
+extern "C" int tlbm_batch_get_staged(tlbm_batch_t b, int* consumer_warps, int* stages, long long* tiles) {
+    if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
+    if (consumer_warps) *consumer_warps = b->staged_nc;
+    if (stages) *stages = b->staged_nc ? b->staged_stages : 0;
+    if (tiles) *tiles = b->staged_nc ? b->staged_tiles : 0;
+    return TLBM_OK;
+}
+
 extern "C" int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* block_x, int* block_y,
                                       int* graph_steps) {
     if (!b) return bfail(nullptr, TLBM_ERR_ARG, "NULL batch");
@@ -646,7 +752,7 @@ extern "C" int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* 
 // Tuned launch shapes of this process, per (lattice, storage, collision form,
 // size class = floor(log2(total nodes))).
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int>, std::array<int, 5>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int>, std::array<int, 6>> g_tune_cache;
 
 static std::tuple<int, int, int, int> tune_key(tlbm_batch_t b) {
     long long nodes = 0;
@@ -673,6 +779,8 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
             b->by = it->second[2];
             b->rows = it->second[3];
             b->tpb = it->second[4];
+            if (it->second[5] > 0 && staged_possible(b)) return batch_set_staged(b, it->second[5], 0);
+            b->staged_nc = 0;
             return upload_tables(b);
         }
     }
@@ -680,6 +788,7 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
     const int vecs[] = {8, 4, 2, 1};
     const int shapes[][2] = {{32, 1}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}};
     const int keep_vec = b->vec, keep_bx = b->bx, keep_by = b->by, keep_rows = b->rows;
+    b->staged_nc = 0;  // the register-kernel shapes first
     float best = 1e30f;
     int bv = keep_vec, bbx = keep_bx, bby = keep_by, brows = keep_rows;
     cudaEvent_t e0, e1;
@@ -752,13 +861,41 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
         }
         b->tpb = btpb;
     }
+    // the staged form (4 or the most consumer warps), against the best register shape
+    int bnc = 0;
+    if (rc == TLBM_OK && staged_possible(b) && (rc = upload_tables(b)) == TLBM_OK) {
+        const int ncs[] = {4, b->dim == 3 ? 7 : 8};
+        for (int nc : ncs) {
+            if (batch_set_staged(b, nc, 0) != TLBM_OK) {
+                b->err[0] = 0;
+                continue;
+            }
+            cudaError_t e = launch_batch(b, b->parity, b->stream);  // warm
+            cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_batch(b, b->parity, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            b->launches += reps + 1;
+            if (ms < best) {
+                best = ms;
+                bnc = nc;
+            }
+        }
+        b->staged_nc = 0;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc == TLBM_OK) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[tune_key(b)] = {bv, bbx, bby, brows, btpb};
+        g_tune_cache[tune_key(b)] = {bv, bbx, bby, brows, btpb, bnc};
     }
-    int rc2 = upload_tables(b);
+    int rc2 = bnc > 0 ? batch_set_staged(b, bnc, 0) : upload_tables(b);
     return rc != TLBM_OK ? rc : rc2;
 }
 
@@ -803,6 +940,7 @@ extern "C" int tlbm_batch_status(tlbm_batch_t b, int* diverged) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "status read: %s", cudaGetErrorString(e));
         if (gs.status) return bfail(b, TLBM_ERR_TIMEOUT, "a persistent launch gave up waiting at a grid barrier");
+        if (gs.staged_status) return bfail(b, TLBM_ERR_TIMEOUT, "a staged step gave up waiting for its copies");
     }
     for (int i = 0; i < b->n; ++i) {
         int rc = tlbm_status(b->inst[i], &diverged[i], nullptr);

@@ -120,6 +120,9 @@ _SIGS = {
     "tlbm_batch_set_variant": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "tlbm_batch_get_variant": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
     "tlbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
+    "tlbm_batch_set_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "tlbm_batch_get_staged": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_longlong)]),
     "tlbm_batch_set_persistent": (C.c_int, [C.c_void_p, C.c_int]),
     "tlbm_batch_instance": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "tlbm_batch_nusselt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -606,6 +609,16 @@ def tlbm_batch_get_variant(b):
     return tuple(x.value for x in v)
 
 
+def tlbm_batch_set_staged(b, consumer_warps: int = 8, stages: int = 0):
+    _bcheck(b, lib().tlbm_batch_set_staged(b, int(consumer_warps), int(stages)))
+
+
+def tlbm_batch_get_staged(b):
+    nc, ns, tiles = C.c_int(), C.c_int(), C.c_longlong()
+    _bcheck(b, lib().tlbm_batch_get_staged(b, C.byref(nc), C.byref(ns), C.byref(tiles)))
+    return nc.value, ns.value, tiles.value
+
+
 def tlbm_batch_autotune(b, trials: int = 5):
     _bcheck(b, lib().tlbm_batch_autotune(b, int(trials)))
 
@@ -714,6 +727,15 @@ class Batch:
 
     def autotune(self, trials=5):
         tlbm_batch_autotune(self.b, trials)
+
+    def set_staged(self, consumer_warps=8, stages=0):
+        """Shared-memory staged form (consumer_warps 4 or 8 in 2D, 4 or 7 in 3D; 0 off)."""
+        tlbm_batch_set_staged(self.b, consumer_warps, stages)
+
+    @property
+    def staged(self):
+        """(consumer warps, stages, tiles per step); (0, 0, 0) for the register kernels."""
+        return tlbm_batch_get_staged(self.b)
 
     def set_persistent(self, steps_per_launch):
         tlbm_batch_set_persistent(self.b, steps_per_launch)

@@ -174,3 +174,84 @@ def test_batch_pipelined_rows_equal_one_row(T, lattice, prec):
         assert np.array_equal(fa, fb) and np.array_equal(ga, gb), k
     a.close()
     b.close()
+
+
+_STAGED_CELLS = {
+    # ragged rows, rows cut into several segments (600 > 8 x 64, 300 > 4 x 64)
+    0: [(33, 36, 1, 3e5, 0.71, 0.1, 21), (65, 40, 1, 1e6, 7.0, 0.1, 22), (300, 23, 1, 2e5, 0.71, 0.1, 23),
+        (600, 9, 1, 5e5, 7.0, 0.1, 24)],
+    1: [(9, 11, 7, 1e5, 0.71, 0.1, 25), (17, 8, 9, 3e5, 7.0, 0.1, 26), (300, 5, 4, 1e6, 0.71, 0.1, 27)],
+}
+
+
+@pytest.mark.parametrize("lattice,prec,nc", [(0, 1, 4), (0, 1, 8), (0, 2, 4), (0, 2, 8), (0, 3, 8), (1, 1, 7),
+                                             (1, 2, 4), (1, 2, 7), (1, 3, 7)])
+def test_staged_batch_equals_single_staged_cells(T, lattice, prec, nc):
+    """The staged batch form (one producer/consumer pipeline over the tiles of
+    every instance) steps each instance bitwise as the single-cell staged kernel
+    steps that cell alone: ragged rows, rows cut into several segments, 3D
+    instances, 37 steps (two CUDA-graph blocks and single launches), and for
+    16-bit storage the stochastic rounding keyed by each instance's own step
+    count."""
+    inst = _STAGED_CELLS[lattice]
+    b = T.Batch(inst, lattice=lattice, precision=prec)
+    b.set_staged(nc)
+    assert b.staged[0] == nc and b.staged[1] >= 2
+    b.init(1e-3)
+    b.step(37)
+    assert b.status() == [False] * len(inst)
+    for k, (nx, ny, nz, Ra, Pr, Ma, seed) in enumerate(inst):
+        s = T.Sim(nx, ny, nz, lattice=lattice, Ra=Ra, Pr=Pr, Ma=Ma, precision=prec)
+        s.set_staged(0, 0)
+        s.init(seed, 1e-3)
+        s.step(37)
+        (fb, gb), (fs, gs) = b.get_populations(k), s.get_populations()
+        assert np.array_equal(fb, fs) and np.array_equal(gb, gs), k
+        s.close()
+    # an explicit register-kernel shape turns the staged form off
+    b.set_variant(0, 0, 0, 0, 16)
+    assert b.staged == (0, 0, 0)
+    b.close()
+
+
+def test_staged_batch_rejects_what_it_cannot_run(T):
+    inst = _STAGED_CELLS[0][:2]
+    b = T.Batch(inst, lattice=0, precision=0)  # FP64
+    with pytest.raises(T.TlbmError) as ei:
+        b.set_staged(8)
+    assert ei.value.code == T.TLBM_ERR_UNSUPPORTED
+    c = T.Batch(inst, lattice=0, precision=2)
+    with pytest.raises(T.TlbmError) as ei:
+        c.set_staged(7)  # 4 or 8 in 2D
+    assert ei.value.code == T.TLBM_ERR_ARG
+    c.set_persistent(4)
+    with pytest.raises(T.TlbmError) as ei:
+        c.set_staged(8)
+    assert ei.value.code == T.TLBM_ERR_UNSUPPORTED
+    b.close()
+    c.close()
+
+
+def test_staged_batch_wait_times_out_and_recovers(T):
+    inst = _STAGED_CELLS[0]
+    b = T.Batch(inst, lattice=0, precision=2)
+    b.set_staged(8)
+    b.set_wait_limit(0)
+    b.init(1e-3)
+    b.step(6)
+    with pytest.raises(T.TlbmError) as ei:
+        b.status()
+    assert ei.value.code == T.TLBM_ERR_TIMEOUT
+    b.set_wait_limit(0.5)
+    b.init(1e-3)
+    b.step(20)
+    assert b.status() == [False] * len(inst)
+    ref = T.Batch(inst, lattice=0, precision=2)
+    ref.set_staged(8)
+    ref.init(1e-3)
+    ref.step(20)
+    for k in range(len(inst)):
+        (fa, ga), (fb, gb) = b.get_populations(k), ref.get_populations(k)
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), k
+    b.close()
+    ref.close()
