@@ -540,6 +540,8 @@ def main(argv=None):
     ap.add_argument("--log-ra", type=float, nargs=2, default=(6.0, 8.0), help="log10 Ra range of the draws")
     ap.add_argument("--input", default="both", choices=["coords", "coarse", "both"])
     ap.add_argument("--out", default="", help="write the full result (per-draw steps and Nu series), JSON")
+    ap.add_argument("--out-compact", default="",
+                    help="write the result without the Nu series, with the command and the device, JSON")
     ap.add_argument("--save-data", default="", help="write the generated training targets (.npz)")
     ap.add_argument("--load-data", default="", help="reuse training targets written by --save-data")
     ap.add_argument("--time-layers", action="store_true",
@@ -598,6 +600,23 @@ def main(argv=None):
         with open(args.out, "w") as fh:
             fh.write(json.dumps(res))
     del res["series"]
+    if args.out_compact:
+        props = torch.cuda.get_device_properties(0)
+        given = list(argv if argv is not None else sys.argv[1:])
+        kept = []  # the command without the output paths
+        while given:
+            a = given.pop(0)
+            if a in ("--out", "--out-compact", "--save-data", "--load-data"):
+                if given:
+                    given.pop(0)
+                continue
+            if a.split("=", 1)[0] in ("--out", "--out-compact", "--save-data", "--load-data"):
+                continue
+            kept.append(a)
+        compact = dict(res, command=" ".join(["python -m paper_2211_03160_gb300.surrogate"] + kept),
+                       hardware=f"{props.name} (sm_{props.major}{props.minor}), FP32 storage for every run")
+        with open(args.out_compact, "w") as fh:
+            fh.write(json.dumps(compact, indent=1))
     print(json.dumps(res))
     return 0
 
