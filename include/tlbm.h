@@ -369,7 +369,8 @@ TLBM_API void tlbm_batch_destroy(tlbm_batch_t b);
  * Layers of a small convolutional surrogate that predicts a statistically
  * steady T/u/v field from (Ra, Pr) to start the solver from (no counterpart in
  * the paper).  3x3 convolutions, stride 1, zero padding 1, NCHW, at most 32
- * channels; BF16 operands on the tensor cores, FP32 accumulation.  All pointers
+ * channels; BF16 operands on the 5th-generation tensor cores (tcgen05.mma),
+ * FP32 accumulation in tensor memory.  All pointers
  * are device pointers owned by the caller; every call is asynchronous on
  * `stream` (a cudaStream_t, NULL = legacy stream) and returns TLBM_ERR_ARG for
  * bad shapes or NULL pointers. */

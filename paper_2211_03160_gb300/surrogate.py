@@ -473,7 +473,7 @@ def summarize(ev) -> dict:
 def time_layers(batch: int = 48, n: int = COARSE, reps: int = 20, warmup: int = 3):
     """CUDA-event timings (ms per call, median over reps) of the 32 -> 32
     channel layer at the training batch: forward (tcgen05), data gradient
-    (tcgen05) and weight gradient (mma.sync), each with the FLOPs of its GEMM
+    (tcgen05) and weight gradient (tcgen05), each with the FLOPs of its GEMM
     (2 x pixels x 32 x 288) as TFLOP/s and its compulsory HBM bytes as GB/s."""
     import torch
 

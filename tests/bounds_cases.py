@@ -1,6 +1,6 @@
 """The cases of the bounds test: every step variant, storage precision and wall
 configuration on small and ragged cells, the in-place scheme, the batched
-ensemble (flattened and persistent), the population transfers, checkpoints and
+ensemble (flattened, persistent and staged, 2D and 3D), the population transfers, checkpoints and
 the reductions.  run() returns, per case, a digest of the final state and of
 the reductions, and (with the bounds-checked library) the number of accesses
 that left the population buffers.
@@ -98,21 +98,27 @@ def run(T, tmp_dir):
         s.step(2)
         _finish(T, s, out, f"{lattice}-{'x'.join(map(str, shape))}-w{walls}-p{pm}-transfers")
         s.close()
-    # the batched ensemble, flattened and persistent
-    inst = [(33, 33, 1, 1e5, 0.71, 0.1, 1), (65, 41, 1, 3e5, 7.0, 0.1, 2), (17, 17, 1, 1e6, 0.71, 0.1, 3)]
-    for prec in (FP32, FP16):
-        for persist in (0, 4):
-            b = T.Batch(inst, lattice=D2, precision=prec)
-            if persist:
-                b.set_persistent(persist)
-            b.init(1e-3)
-            b.step(9)
-            for k in range(len(inst)):
-                f, g = b.get_populations(k)
-                h = T.tlbm_batch_instance(b.b, k)
-                out[f"batch-q{prec}-p{persist}-{k}"] = {"hash": _digest(f, g), "red": [],
-                                                        "violations": _violations(T, h)}
-            b.close()
+    # the batched ensemble: flattened, persistent and staged (4 and the most consumer warps;
+    # rows of the 300-node cell cut into two segments with 4 warps)
+    inst2 = [(33, 33, 1, 1e5, 0.71, 0.1, 1), (65, 41, 1, 3e5, 7.0, 0.1, 2), (17, 17, 1, 1e6, 0.71, 0.1, 3),
+             (300, 9, 1, 2e5, 7.0, 0.1, 4)]
+    inst3 = [(9, 11, 7, 1e5, 0.71, 0.1, 5), (17, 8, 9, 3e5, 7.0, 0.1, 6), (300, 5, 4, 1e6, 0.71, 0.1, 7)]
+    cases = [(D2, inst2, prec, mode) for prec in (FP32, FP16) for mode in ("flat", "persist", "staged4", "staged8")]
+    cases += [(D3, inst3, FP16, mode) for mode in ("flat", "staged4", "staged7")]
+    for lattice, inst, prec, mode in cases:
+        b = T.Batch(inst, lattice=lattice, precision=prec)
+        if mode == "persist":
+            b.set_persistent(4)
+        elif mode.startswith("staged"):
+            b.set_staged(int(mode[len("staged"):]))
+        b.init(1e-3)
+        b.step(9)
+        for k in range(len(inst)):
+            f, g = b.get_populations(k)
+            h = T.tlbm_batch_instance(b.b, k)
+            out[f"batch-{lattice}-q{prec}-{mode}-{k}"] = {"hash": _digest(f, g), "red": [],
+                                                          "violations": _violations(T, h)}
+        b.close()
     return out
 
 
