@@ -333,9 +333,11 @@ TLBM_API int tlbm_batch_set_rows(tlbm_batch_t b, int rows);
 TLBM_API int tlbm_batch_get_rows(tlbm_batch_t b, int* rows);
 /* Shared-memory staged form of the flattened launch (the single-cell staged
  * kernel's pipeline, tlbm_set_staged, over the tiles of every instance):
- * consumer_warps 4 or 8 in 2D, 4 or 7 in 3D (tiles of up to 64 x that many
- * nodes; each instance's rows are cut into the fewest equal segments), 0 turns
- * it off; stages 0 chooses the tiles in flight per block, else 2 .. 8.  FP32,
+ * consumer_warps 4 or 8 in 2D, 4 or 7 in 3D, 0 turns it off; a tile is a
+ * stretch of 64 x consumer_warps elements of one z-plane's interior rows of an
+ * instance, which lie contiguously at the row pitch (tiles run over row ends;
+ * the lanes on padding and ghost columns idle); stages 0 chooses the tiles in
+ * flight per block, else 2 .. 8.  FP32,
  * FP16 or BF16 storage with two-relaxation-time rates in every instance
  * (TLBM_ERR_UNSUPPORTED otherwise, and for the persistent form).
  * tlbm_batch_set_variant turns it off; tlbm_batch_autotune times it against
@@ -345,9 +347,9 @@ TLBM_API int tlbm_batch_set_staged(tlbm_batch_t b, int consumer_warps, int stage
 /* The staged form's consumer warps (0: off), stages and tiles per step. */
 TLBM_API int tlbm_batch_get_staged(tlbm_batch_t b, int* consumer_warps, int* stages, long long* tiles);
 /* Time the compiled launch shapes (nodes per thread x rows per thread x block
- * shape, then tiles per block, then the staged form where it applies; trials
- * launches each) on the bound state and keep the fastest.  The state is not
- * changed. */
+ * shape, then tiles per block, then the staged form where it applies: 4 or the
+ * most consumer warps x 2 or 3 stages; trials launches each) on the bound
+ * state and keep the fastest.  The state is not changed. */
 TLBM_API int tlbm_batch_autotune(tlbm_batch_t b, int trials);
 /* (trials < 0: reuse the shape this process tuned for the same lattice, storage,
  * collision form and size class floor(log2(total nodes)), if any.) */

@@ -369,17 +369,16 @@ static void build_tables(tlbm_batch_t b, std::vector<KParams>& kps, std::vector<
         ins[i].gx = gx;
         ins[i].gy = gy;
         block0 += (long long)gx * gy * h->nz;
-        // staged form: rows cut into the fewest segments of at most 64 NC nodes,
-        // of equal width rounded up to the 16-byte copy granule
+        // staged form: stretches of 64 NC elements of each z-plane's interior
+        // rows (ny P elements, contiguous; a multiple of the 16-byte copy granule)
         ins[i].stile0 = stile0;
         ins[i].stw = ins[i].stpr = 0;
         if (b->staged_nc > 0) {
-            const int twmax = 64 * b->staged_nc, A = 16 / (int)h->elem;
-            const int segs = (h->nx + twmax - 1) / twmax;
-            const int tw = ((h->nx + segs - 1) / segs + A - 1) / A * A;
+            const long long run = (long long)h->ny * h->kp.L.P;
+            const int tw = (int)std::min<long long>(64 * b->staged_nc, run);
             ins[i].stw = tw;
-            ins[i].stpr = (h->nx + tw - 1) / tw;
-            stile0 += (long long)h->ny * h->nz * ins[i].stpr;
+            ins[i].stpr = (int)((run + tw - 1) / tw);
+            stile0 += (long long)h->nz * ins[i].stpr;
         }
     }
     b->total_blocks = block0;
@@ -752,7 +751,7 @@ extern "C" int tlbm_batch_get_variant(tlbm_batch_t b, int* vec, int* form, int* 
 // Tuned launch shapes of this process, per (lattice, storage, collision form,
 // size class = floor(log2(total nodes))).
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int>, std::array<int, 6>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int>, std::array<int, 7>> g_tune_cache;
 
 static std::tuple<int, int, int, int> tune_key(tlbm_batch_t b) {
     long long nodes = 0;
@@ -779,7 +778,7 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
             b->by = it->second[2];
             b->rows = it->second[3];
             b->tpb = it->second[4];
-            if (it->second[5] > 0 && staged_possible(b)) return batch_set_staged(b, it->second[5], 0);
+            if (it->second[5] > 0 && staged_possible(b)) return batch_set_staged(b, it->second[5], it->second[6]);
             b->staged_nc = 0;
             return upload_tables(b);
         }
@@ -861,12 +860,15 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
         }
         b->tpb = btpb;
     }
-    // the staged form (4 or the most consumer warps), against the best register shape
-    int bnc = 0;
+    // the staged form (4 or the most consumer warps, 2 or 3 stages), against the
+    // best register shape
+    int bnc = 0, bns = 0;
     if (rc == TLBM_OK && staged_possible(b) && (rc = upload_tables(b)) == TLBM_OK) {
         const int ncs[] = {4, b->dim == 3 ? 7 : 8};
-        for (int nc : ncs) {
-            if (batch_set_staged(b, nc, 0) != TLBM_OK) {
+        const int nss[] = {2, 3};
+        for (int nc : ncs)
+        for (int ns : nss) {
+            if (batch_set_staged(b, nc, ns) != TLBM_OK) {
                 b->err[0] = 0;
                 continue;
             }
@@ -885,6 +887,7 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
             if (ms < best) {
                 best = ms;
                 bnc = nc;
+                bns = ns;
             }
         }
         b->staged_nc = 0;
@@ -893,9 +896,9 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
     cudaEventDestroy(e1);
     if (rc == TLBM_OK) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[tune_key(b)] = {bv, bbx, bby, brows, btpb, bnc};
+        g_tune_cache[tune_key(b)] = {bv, bbx, bby, brows, btpb, bnc, bns};
     }
-    int rc2 = bnc > 0 ? batch_set_staged(b, bnc, 0) : upload_tables(b);
+    int rc2 = bnc > 0 ? batch_set_staged(b, bnc, bns) : upload_tables(b);
     return rc != TLBM_OK ? rc : rc2;
 }
 

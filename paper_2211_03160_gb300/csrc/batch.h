@@ -12,12 +12,12 @@ struct BatchInst {
     long long block0;    // first flattened block of the instance
     int gx, gy;          // blocks along x and y of the instance (z: nz)
     long long stile0;    // first tile of the instance in the staged form
-    int stw, stpr;       // staged form: tile width (nodes) and tiles per row
+    int stw, stpr;       // staged form: tile length (elements of a plane's interior rows) and tiles per z-plane
 };
 
 // Staged form: the tiles of all instances, stage count and status word.
 struct BatchStagedInfo {
-    long long tiles;             // sum over instances of ny nz stpr
+    long long tiles;             // sum over instances of nz stpr
     int stages;                  // tiles in flight per CTA, 2 <= stages <= TILE_MAX_STAGES
     int* status;                 // set to 1 by a block that gave up waiting
     unsigned long long wait_ns;  // wait limit for a copy or a free stage

@@ -3,8 +3,11 @@
 // each tile's source row segments global -> shared with cp.async.bulk on an
 // mbarrier ring, NC consumer warps collide two nodes per thread) walking the
 // tiles of every instance.  Tiles are numbered instance by instance: instance i
-// owns tiles [stile0_i, stile0_{i+1}), row segments of stw_i nodes, stpr_i per
-// row.  The producer puts each tile's instance and that instance's step count
+// owns tiles [stile0_i, stile0_{i+1}), stpr_i per z-plane.  A tile is a stretch
+// of stw_i elements of a z-plane's interior rows, which lie contiguously at the
+// row pitch P (each row's ghost columns sit in its padding): tiles run over row
+// ends, so that every tile but a plane's last is full whatever the width of
+// the cell; the lanes that fall on padding idle.  The producer puts each tile's instance and that instance's step count
 // (the stochastic-rounding salt of 16-bit storage) into the stage header next to
 // the tile's coordinates; the consumers read the instance's parameters from the
 // global table (read-only, the same block of ~1.2 KB for every tile of an
@@ -33,7 +36,7 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 7 ? 128 : 168))
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
     uint64_t* empty = full + TILE_MAX_STAGES;
-    int4* head = reinterpret_cast<int4*>(empty + TILE_MAX_STAGES);  // per stage: x0, y, z, width
+    int4* head = reinterpret_cast<int4*>(empty + TILE_MAX_STAGES);  // per stage: x, y of e0, z, length
     int2* hinst = reinterpret_cast<int2*>(head + TILE_MAX_STAGES);  // per stage: instance, step count
     S* stages = reinterpret_cast<S*>(smem_raw + 512);
     const int NS = si.stages;
@@ -65,29 +68,31 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 7 ? 128 : 168))
             }
             const KParams& p = kps[i];
             const long long local = t - inst[i].stile0;
-            const int tpr = inst[i].stpr, tws = inst[i].stw;
-            const int r = (int)(local / tpr);
-            const int x0 = (int)(local - (long long)r * tpr) * tws;
-            const int ny = p.L.ny;
-            const int z = r / ny, y = r - z * ny;
-            const int tw = min(tws, p.L.nx - x0);
+            const int tpp = inst[i].stpr, tws = inst[i].stw;
+            const int z = (int)(local / tpp);
+            const int e0 = (int)(local - (long long)z * tpp) * tws;
+            const int P = p.L.P;
+            const int tw = min(tws, p.L.ny * P - e0);
             const S* src = static_cast<const S*>(inst[i].buf[parity]);
-            const int lo = ex == 1 ? x0 - A : x0;
-            const int end = (x0 + tw + (ex == -1 ? 1 : 0) + A - 1) / A * A;
+            // population `lane` needs e0 - 1 only if e_x = +1 and e0 + tw only
+            // if e_x = -1; its copy starts and ends on 16-byte boundaries
+            const int lo = ex == 1 ? e0 - A : e0;
+            const int end = (e0 + tw + (ex == -1 ? 1 : 0) + A - 1) / A * A;
             const uint32_t bytes = lane < Q ? (uint32_t)(end - lo) * (uint32_t)sizeof(S) : 0u;
             const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
             if (lane == 0) {
                 // the instance's step count; its first tile's producer advances it
                 const uint32_t tc = step_count<S>(src, 0);
                 advance_count<S>(static_cast<S*>(const_cast<void*>(inst[i].buf[parity ^ 1])), 0, tc, local == 0);
-                head[s] = make_int4(x0, y, z, tw);
+                const int y0 = e0 / P;  // the tile's first element: row y0, column e0 - y0 P
+                head[s] = make_int4(e0 - y0 * P, y0, z, tw);
                 hinst[s] = make_int2(i, (int)tc);
                 mbar_arrive_expect_tx(&full[s], total);
             }
             __syncwarp();
             if (lane < Q)
-                bulk_copy_g2s(stages + s * STAGE + lane * LW + (lo - (x0 - A)),
-                              TLBM_DBG(p, (src + p.L.row(y, z) + p.loff[lane] + lo), 0, (int)(bytes / sizeof(S))),
+                bulk_copy_g2s(stages + s * STAGE + lane * LW + (lo - (e0 - A)),
+                              TLBM_DBG(p, (src + p.L.row(0, z) + p.loff[lane] + lo), 0, (int)(bytes / sizeof(S))),
                               bytes, &full[s]);
             if (++s == NS) {
                 s = 0;
@@ -111,9 +116,15 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 7 ? 128 : 168))
         }
         const int4 hd = head[s];
         const int2 hi = hinst[s];
-        const int x0 = hd.x, y = hd.y, z = hd.z, tw = hd.w;
+        const int z = hd.z, tw = hd.w;
         const KParams& p = kps[hi.x];
-        const bool active = xr < tw;
+        int x = hd.x + xr, y = hd.y;  // this thread's first element, carried over row ends
+        while (x >= p.L.P) {
+            x -= p.L.P;
+            ++y;
+        }
+        const bool active = xr < tw && x < p.L.nx;
+        const bool both = xr + 1 < tw && x + 1 < p.L.nx;
         const S* st = stages + s * STAGE;
         const float inv_scale = ScaleOf<float>::inv(p);
         float2 fd[QF], gd[QG];
@@ -149,8 +160,8 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 7 ? 128 : 168))
         const float scale = ScaleOf<float>::s(p);
         collide_trt_v<DIM, float2, collide_scaled<S, true>, true>(fd, gd, p);
         S* dst = static_cast<S*>(const_cast<void*>(inst[hi.x].buf[parity ^ 1]));
-        S* own = dst + p.L.row(y, z) + x0 + xr;
-        if (xr + 1 < tw) {
+        S* own = dst + p.L.row(y, z) + x;
+        if (both) {
             static_for<QF>([&](auto ii) {
                 constexpr int q = decltype(ii)::value;
                 *reinterpret_cast<S2*>(TLBM_DBG(p, (own + p.soff[q]), 0, 2)) =
@@ -176,7 +187,7 @@ __global__ void __maxnreg__(DIM == 2 && NC == 8 ? 72 : (NC == 7 ? 128 : 168))
         for (int q = 0; q < QF; ++q) { f2[q][0] = fd[q].x; f2[q][1] = fd[q].y; }
 #pragma unroll
         for (int q = 0; q < QG; ++q) { g2[q][0] = gd[q].x; g2[q][1] = gd[q].y; }
-        wall_writes<DIM, S, 2, float, KS>(dst, p, x0 + xr, y, z, f2, g2, salt);
+        wall_writes<DIM, S, 2, float, KS>(dst, p, x, y, z, f2, g2, salt);
     }
 }
 
