@@ -348,7 +348,7 @@ TLBM_API int tlbm_batch_set_staged(tlbm_batch_t b, int consumer_warps, int stage
 TLBM_API int tlbm_batch_get_staged(tlbm_batch_t b, int* consumer_warps, int* stages, long long* tiles);
 /* Time the compiled launch shapes (nodes per thread x rows per thread x block
  * shape, then tiles per block, then the staged form where it applies: 4 or the
- * most consumer warps x 2 or 3 stages; trials launches each) on the bound
+ * most consumer warps x 2 to 4 stages; trials launches each) on the bound
  * state and keep the fastest.  The state is not changed. */
 TLBM_API int tlbm_batch_autotune(tlbm_batch_t b, int trials);
 /* (trials < 0: reuse the shape this process tuned for the same lattice, storage,

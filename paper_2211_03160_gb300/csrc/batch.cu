@@ -860,12 +860,12 @@ extern "C" int tlbm_batch_autotune(tlbm_batch_t b, int trials) {
         }
         b->tpb = btpb;
     }
-    // the staged form (4 or the most consumer warps, 2 or 3 stages), against the
+    // the staged form (4 or the most consumer warps, 2 to 4 stages), against the
     // best register shape
     int bnc = 0, bns = 0;
     if (rc == TLBM_OK && staged_possible(b) && (rc = upload_tables(b)) == TLBM_OK) {
         const int ncs[] = {4, b->dim == 3 ? 7 : 8};
-        const int nss[] = {2, 3};
+        const int nss[] = {2, 3, 4};
         for (int nc : ncs)
         for (int ns : nss) {
             if (batch_set_staged(b, nc, ns) != TLBM_OK) {
