@@ -225,3 +225,45 @@ def test_staged_query_and_batch_rows_on_host(T):
         assert T.tlbm_batch_get_rows(b) == 2
     finally:
         T.tlbm_batch_destroy(b)
+
+
+def test_staged_batch_arguments_on_host(T):
+    """tlbm_batch_set_staged checks its arguments before any device call:
+    consumer warps 4 or 8 in 2D (4 or 7 in 3D), stages 0 or 2..8, no FP64
+    storage, not with the persistent form; a fresh batch reports the register
+    kernels."""
+    b = T.tlbm_batch_create([(33, 33, 1, 1e5, 0.71, 0.1, 1)], 0, T.TLBM_FP16_OFFSET)
+    try:
+        assert T.tlbm_batch_get_staged(b) == (0, 0, 0)
+        for nc, ns, code in ((7, 0, T.TLBM_ERR_ARG), (5, 0, T.TLBM_ERR_ARG), (-1, 0, T.TLBM_ERR_ARG),
+                             (8, 1, T.TLBM_ERR_ARG), (4, 9, T.TLBM_ERR_ARG)):
+            with pytest.raises(T.TlbmError) as ei:
+                T.tlbm_batch_set_staged(b, nc, ns)
+            assert ei.value.code == code, (nc, ns)
+        T.tlbm_batch_set_staged(b, 0, 0)  # off: nothing to check
+        assert T.tlbm_batch_get_staged(b) == (0, 0, 0)
+    finally:
+        T.tlbm_batch_destroy(b)
+    b3 = T.tlbm_batch_create([(9, 11, 7, 1e5, 0.71, 0.1, 1)], 1, T.TLBM_BF16_OFFSET)
+    try:
+        with pytest.raises(T.TlbmError) as ei:
+            T.tlbm_batch_set_staged(b3, 8, 0)  # 4 or 7 in 3D
+        assert ei.value.code == T.TLBM_ERR_ARG
+    finally:
+        T.tlbm_batch_destroy(b3)
+    b64 = T.tlbm_batch_create([(33, 33, 1, 1e5, 0.71, 0.1, 1)], 0, T.TLBM_FP64)
+    try:
+        with pytest.raises(T.TlbmError) as ei:
+            T.tlbm_batch_set_staged(b64, 8, 0)
+        assert ei.value.code == T.TLBM_ERR_UNSUPPORTED
+    finally:
+        T.tlbm_batch_destroy(b64)
+
+
+def test_conv_weight_operand_size(T):
+    """The packed convolution weights hold 9 taps x ceil(cin / 16) tiles of
+    32 x 16 BF16 elements; channel counts outside 1..32 have no operand."""
+    for cin, n in ((1, 4608), (5, 4608), (16, 4608), (17, 9216), (32, 9216)):
+        assert T.tlbm_conv3x3_weight_elems(cin) == n
+    for bad in (0, -3, 33):
+        assert T.tlbm_conv3x3_weight_elems(bad) == 0
