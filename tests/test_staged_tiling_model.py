@@ -8,6 +8,7 @@ lie in one row, and that every population's copy starts and ends on a
 16-byte boundary inside the plane's ghost rows."""
 import pytest
 
+
 def pitch(nx):
     """The row pitch of the population layout (tlbm_bind_memory): 32 ceil((nx + 16) / 32)."""
     return 32 * ((nx + 16 + 31) // 32)
