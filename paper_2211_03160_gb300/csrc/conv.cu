@@ -4,9 +4,10 @@
 // Convolutions are implicit GEMMs on the tensor cores, BF16 operands with FP32
 // accumulation:
 //   forward   out[b][m][p] = bias[m] + sum_k A[m][k] col(x)[k][b, p]
-//             with A = W reshaped to [Cout][Cin*9] and col(x) the 3x3 patches,
-//             on the 5th-generation tensor cores (tcgen05.mma, accumulator in
-//             tensor memory);
+//             with A[m][9c + 3di + dj] = W[m][c][di][dj] (stored in the
+//             kernel's shared-memory tile order, pack_weights_kernel) and
+//             col(x) the 3x3 patches, on the 5th-generation tensor cores
+//             (tcgen05.mma, accumulator in tensor memory);
 //   data grad the same kernel with A = W transposed and flipped, x = dL/dy;
 //   weight grad  dW[m][n] = sum_{b,p} dy[b][m][p] col(x)[n][b, p], per-CTA
 //             partials over tiles of pixels summed in a fixed order
